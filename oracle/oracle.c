@@ -1,0 +1,291 @@
+/*
+ * oracle.c — TEST INFRASTRUCTURE.  A plain, serial, obviously-correct CPU
+ * statement of what the traversal path computes.  Only the tests, the smoke
+ * check and the benchmark's CPU-baseline leg may load it; the product path
+ * never does.  It shares no code, header, table or helper with the CUDA
+ * library.
+ *
+ * What it computes (problem statements of the benchmark section, §4):
+ *   - BFS: D[v] = hop distance from src, "infinity" if unreachable.
+ *   - Integral-weight SSSP (weighted BFS): D[v] = shortest-path distance with
+ *     positive integer edge weights, "infinity" if unreachable.
+ * Both results are unique, so the oracle computes the plain definitions —
+ * a FIFO-queue BFS and a binary-heap Dijkstra — with no frontier or bucket
+ * machinery.  Floyd–Warshall is included as a brute-force check for tiny
+ * graphs.  Infinity is INT32_MAX; unreachable parents are -1; the parent of
+ * the source is the source itself.
+ *
+ * The validators state the invariants that any correct BFS tree / shortest-
+ * path labelling satisfies (used where several outputs are correct, e.g.
+ * parents chosen by whichever test-and-set wins, Alg. 1).
+ *
+ * Inputs: symmetric CSR, uint32 offsets off[0..n], int32 targets tgt[0..m),
+ * optional uint32 weights w[0..m).
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_INF INT32_MAX
+
+/* ------------------------------------------------------------------ BFS */
+/* Hop distances and one BFS tree (FIFO order, neighbours in CSR order).
+ * Returns the number of reached vertices, or -1 on a bad argument. */
+int64_t or_bfs(int32_t n, const uint32_t *off, const int32_t *tgt, int32_t src,
+               int32_t *dist, int32_t *parent) {
+  if (n <= 0 || src < 0 || src >= n) return -1;
+  for (int32_t v = 0; v < n; v++) {
+    dist[v] = OR_INF;
+    if (parent) parent[v] = -1;
+  }
+  int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+  if (!queue) return -1;
+  int64_t head = 0, tail = 0;
+  dist[src] = 0;
+  if (parent) parent[src] = src;
+  queue[tail++] = src;
+  while (head < tail) {
+    int32_t u = queue[head++];
+    for (uint32_t k = off[u]; k < off[u + 1]; k++) {
+      int32_t v = tgt[k];
+      if (dist[v] == OR_INF) {
+        dist[v] = dist[u] + 1;
+        if (parent) parent[v] = u;
+        queue[tail++] = v;
+      }
+    }
+  }
+  free(queue);
+  return tail;
+}
+
+/* ------------------------------------------------------------- Dijkstra */
+typedef struct {
+  int64_t d;
+  int32_t v;
+} heap_item;
+
+static void heap_push(heap_item *h, int64_t *size, heap_item x) {
+  int64_t i = (*size)++;
+  while (i > 0) {
+    int64_t p = (i - 1) / 2;
+    if (h[p].d <= x.d) break;
+    h[i] = h[p];
+    i = p;
+  }
+  h[i] = x;
+}
+
+static heap_item heap_pop(heap_item *h, int64_t *size) {
+  heap_item top = h[0];
+  heap_item last = h[--(*size)];
+  int64_t i = 0, s = *size;
+  for (;;) {
+    int64_t c = 2 * i + 1;
+    if (c >= s) break;
+    if (c + 1 < s && h[c + 1].d < h[c].d) c++;
+    if (h[c].d >= last.d) break;
+    h[i] = h[c];
+    i = c;
+  }
+  if (s > 0) h[i] = last;
+  return top;
+}
+
+/* Shortest-path distances with non-negative integer weights (int64
+ * accumulation, int32 result).  Binary heap with lazy deletion: a vertex may
+ * be pushed once per improvement; stale pops are skipped.  Returns the number
+ * of reached vertices, -1 on a bad argument, -2 if a distance exceeds int32. */
+int64_t or_dijkstra(int32_t n, const uint32_t *off, const int32_t *tgt, const uint32_t *w,
+                    int32_t src, int32_t *dist) {
+  if (n <= 0 || src < 0 || src >= n || !w) return -1;
+  int64_t m = off[n];
+  int64_t *d = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+  heap_item *h = (heap_item *)malloc(sizeof(heap_item) * (size_t)(m + 1));
+  char *done = (char *)calloc((size_t)n, 1);
+  if (!d || !h || !done) {
+    free(d);
+    free(h);
+    free(done);
+    return -1;
+  }
+  for (int32_t v = 0; v < n; v++) d[v] = INT64_MAX;
+  int64_t size = 0, reached = 0;
+  d[src] = 0;
+  heap_item s0 = {0, src};
+  heap_push(h, &size, s0);
+  while (size > 0) {
+    heap_item it = heap_pop(h, &size);
+    int32_t u = it.v;
+    if (done[u] || it.d != d[u]) continue;
+    done[u] = 1;
+    reached++;
+    for (uint32_t k = off[u]; k < off[u + 1]; k++) {
+      int32_t v = tgt[k];
+      int64_t nd = d[u] + (int64_t)w[k];
+      if (nd < d[v]) {
+        d[v] = nd;
+        heap_item x = {nd, v};
+        heap_push(h, &size, x);
+      }
+    }
+  }
+  int64_t rc = reached;
+  for (int32_t v = 0; v < n; v++) {
+    if (d[v] == INT64_MAX) dist[v] = OR_INF;
+    else if (d[v] >= OR_INF) { dist[v] = OR_INF; rc = -2; }
+    else dist[v] = (int32_t)d[v];
+  }
+  free(d);
+  free(h);
+  free(done);
+  return rc;
+}
+
+/* --------------------------------------------------------- Floyd–Warshall */
+/* All-pairs shortest paths by brute force, for tiny graphs only.  d is
+ * n*n int64, row-major, INT64_MAX = unreachable.  w == NULL means unit
+ * weights (hop distances). */
+int or_floyd_warshall(int32_t n, const uint32_t *off, const int32_t *tgt, const uint32_t *w,
+                      int64_t *d) {
+  if (n <= 0 || n > 4096) return -1;
+  for (int64_t i = 0; i < (int64_t)n * n; i++) d[i] = INT64_MAX;
+  for (int32_t u = 0; u < n; u++) {
+    d[(int64_t)u * n + u] = 0;
+    for (uint32_t k = off[u]; k < off[u + 1]; k++) {
+      int64_t c = w ? (int64_t)w[k] : 1;
+      int64_t *e = &d[(int64_t)u * n + tgt[k]];
+      if (c < *e) *e = c;
+    }
+  }
+  for (int32_t k = 0; k < n; k++)
+    for (int32_t i = 0; i < n; i++) {
+      int64_t dik = d[(int64_t)i * n + k];
+      if (dik == INT64_MAX) continue;
+      for (int32_t j = 0; j < n; j++) {
+        int64_t dkj = d[(int64_t)k * n + j];
+        if (dkj == INT64_MAX) continue;
+        if (dik + dkj < d[(int64_t)i * n + j]) d[(int64_t)i * n + j] = dik + dkj;
+      }
+    }
+  return 0;
+}
+
+/* ------------------------------------------------------------ validators */
+static int has_arc(const uint32_t *off, const int32_t *tgt, int32_t u, int32_t v) {
+  for (uint32_t k = off[u]; k < off[u + 1]; k++)
+    if (tgt[k] == v) return 1;
+  return 0;
+}
+
+/* Error codes written to *code by the validators. */
+enum {
+  OR_OK = 0,
+  OR_BAD_SOURCE = 1,     /* dist[src] != 0 or parent[src] != src */
+  OR_EDGE_GAP = 2,       /* an arc (u,v) with |D[u]-D[v]| > 1 (BFS) or D[v] > D[u]+w (SSSP) */
+  OR_REACH_MISMATCH = 3, /* an arc joining a reached and an unreached vertex */
+  OR_BAD_PARENT = 4,     /* parent out of range, not adjacent, or D[parent] != D[v]-1 */
+  OR_UNREACHED_PARENT = 5, /* unreached vertex with parent != -1 */
+  OR_NO_TIGHT_ARC = 6,   /* reached v != src with no arc u->v where D[u]+w == D[v] */
+  OR_NEGATIVE = 7        /* a negative distance */
+};
+
+/* BFS output invariants: D[src]=0, P[src]=src; for every arc, both ends are
+ * reached or neither, and |D[u]-D[v]| <= 1; for reached v != src, P[v] is a
+ * neighbour of v with D[P[v]] = D[v]-1; unreached v has P[v] = -1.  Together
+ * with D[src]=0 these imply D is exactly the hop distance.  parent may be NULL
+ * (distances only).  Returns -1 if all hold, else the first failing vertex
+ * (code in *code). */
+int64_t or_check_bfs(int32_t n, const uint32_t *off, const int32_t *tgt, int32_t src,
+                     const int32_t *dist, const int32_t *parent, int32_t *code) {
+  *code = OR_OK;
+  if (dist[src] != 0 || (parent && parent[src] != src)) {
+    *code = OR_BAD_SOURCE;
+    return src;
+  }
+  for (int32_t v = 0; v < n; v++) {
+    int32_t dv = dist[v];
+    if (dv < 0) {
+      *code = OR_NEGATIVE;
+      return v;
+    }
+    for (uint32_t k = off[v]; k < off[v + 1]; k++) {
+      int32_t u = tgt[k];
+      int32_t du = dist[u];
+      if ((du == OR_INF) != (dv == OR_INF)) {
+        *code = OR_REACH_MISMATCH;
+        return v;
+      }
+      if (dv != OR_INF && (du - dv > 1 || dv - du > 1)) {
+        *code = OR_EDGE_GAP;
+        return v;
+      }
+    }
+    if (v == src) continue;
+    if (dv == OR_INF) {
+      if (parent && parent[v] != -1) {
+        *code = OR_UNREACHED_PARENT;
+        return v;
+      }
+      continue;
+    }
+    if (parent) {
+      int32_t p = parent[v];
+      if (p < 0 || p >= n || dist[p] != dv - 1 || !has_arc(off, tgt, v, p)) {
+        *code = OR_BAD_PARENT;
+        return v;
+      }
+    } else {
+      /* Without parents, some neighbour must be one level closer. */
+      int ok = 0;
+      for (uint32_t k = off[v]; k < off[v + 1] && !ok; k++)
+        if (dist[tgt[k]] == dv - 1) ok = 1;
+      if (!ok) {
+        *code = OR_NO_TIGHT_ARC;
+        return v;
+      }
+    }
+  }
+  return -1;
+}
+
+/* SSSP output invariants (positive integer weights): D[src]=0; every arc
+ * joins two reached or two unreached vertices and satisfies
+ * D[v] <= D[u] + w(u,v); every reached v != src has a tight arc
+ * D[u] + w(u,v) == D[v].  With positive weights these characterise the
+ * shortest-path distances. */
+int64_t or_check_sssp(int32_t n, const uint32_t *off, const int32_t *tgt, const uint32_t *w,
+                      int32_t src, const int32_t *dist, int32_t *code) {
+  *code = OR_OK;
+  if (dist[src] != 0) {
+    *code = OR_BAD_SOURCE;
+    return src;
+  }
+  for (int32_t v = 0; v < n; v++) {
+    int64_t dv = dist[v];
+    if (dv < 0) {
+      *code = OR_NEGATIVE;
+      return v;
+    }
+    int tight = (v == src);
+    for (uint32_t k = off[v]; k < off[v + 1]; k++) {
+      int32_t u = tgt[k];
+      int64_t du = dist[u];
+      if ((du == OR_INF) != (dv == OR_INF)) {
+        *code = OR_REACH_MISMATCH;
+        return v;
+      }
+      if (dv == OR_INF) continue;
+      if (dv > du + (int64_t)w[k]) {
+        *code = OR_EDGE_GAP;
+        return v;
+      }
+      if (du + (int64_t)w[k] == dv) tight = 1;
+    }
+    if (dv != OR_INF && !tight) {
+      *code = OR_NO_TIGHT_ARC;
+      return v;
+    }
+  }
+  return -1;
+}
