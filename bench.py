@@ -1,0 +1,380 @@
+#!/usr/bin/env python3
+"""Benchmark of the frontier-traversal path on one GB300 (or N replicas).
+
+Default workload (the configuration the headline metric is quoted on):
+weighted BFS (integral-weight SSSP) on a seeded RMAT graph, scale 22, edge
+factor 16, a/b/c/d = .57/.19/.19/.05, symmetrized and deduplicated, uint32
+weights uniform in [1, 22); 8 seeded sources run one at a time.  One step =
+those 8 queries.  Other workloads: --workload bfs-rmat22, bfs-rmat26,
+wbfs-rmat26, bfs-grid, wbfs-grid.
+
+Metric: GTEPS, Graph500 convention: per query, the undirected edges of the
+reached component (sum of reached degrees / 2), summed over queries, over the
+device time.  The graph (~1 GB at scale 22) is larger than L2, so no flush
+is needed between steps.
+
+Prints ONE JSON line.  --impl reference times the oracle (the serial CPU
+reference) on bounded samples of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import graphgen as G  # noqa: E402
+
+INF = 2**31 - 1
+
+WORKLOADS = {
+    "wbfs-rmat22": dict(kind="wbfs", graph="rmat", scale=22, ef=16, w=(1, 22), nsrc=8,
+                        desc="wBFS, RMAT scale 22 ef16, w in [1,22), 8 seeded sources one at a time"),
+    "bfs-rmat22": dict(kind="bfs", graph="rmat", scale=22, ef=16, w=None, nsrc=8,
+                       desc="BFS (dist+parent), RMAT scale 22 ef16, 8 seeded sources"),
+    "bfs-rmat26": dict(kind="bfs", graph="rmat", scale=26, ef=16, w=None, nsrc=4,
+                       desc="BFS (dist+parent), RMAT scale 26 ef16 (~2.1B arcs), 4 seeded sources"),
+    "wbfs-rmat26": dict(kind="wbfs", graph="rmat", scale=26, ef=16, w=(1, 22), nsrc=2,
+                        desc="wBFS, RMAT scale 26 ef16, w in [1,22), 2 seeded sources"),
+    "bfs-grid": dict(kind="bfs", graph="grid", R=4096, C=4096, w=None, nsrc=4,
+                     desc="BFS, 4096x4096 grid, 10% edges deleted, source 0 + 3 seeded"),
+    "wbfs-grid": dict(kind="wbfs", graph="grid", R=4096, C=4096, w=(1, 16), nsrc=4,
+                      desc="wBFS, 4096x4096 grid, 10% deleted, w in [1,16), source 0 + 3 seeded"),
+}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+def make_graph(wl):
+    if wl["graph"] == "rmat":
+        g = G.rmat(wl["scale"], wl["ef"], 0.57, 0.19, 0.19, seed=1, permute=True)
+    else:
+        g = G.grid(wl["R"], wl["C"], 0.1, seed=1)
+    if wl["w"] is not None:
+        G.add_weights(g, wl["w"][0], wl["w"][1], seed=2)
+    return g
+
+
+def make_sources(g, wl, rank=0):
+    k = wl["nsrc"]
+    if wl["graph"] == "grid":
+        s = G.sources(g, k, seed=3 + 1000 * rank)
+        if rank == 0:
+            s[0] = 0
+        return s
+    return G.sources(g, k, seed=3 + 1000 * rank)
+
+
+def traversed_edges(g, dist):
+    """Graph500 TEPS numerator: undirected edges in the reached component."""
+    deg = np.diff(g.off.astype(np.int64))
+    return int(deg[dist != INF].sum() // 2)
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index=0):
+        self.rows = []
+        self.proc = None
+        self.dev = device_index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=3)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def bytes_model(kind, n, st):
+    """Algorithmic bytes of one query (every access counted once, 4 B per
+    word, random or not), from the device statistics of the query."""
+    E, V, R, I = st["edges_scanned"], st["vertices_expanded"], st["relaxations"], st["bucket_inserts"]
+    if kind == "wbfs":
+        # init D + stamp (8n); per frontier vertex q,qoff,off[u] + queue write (20);
+        # per arc tgt,w,D[v] (12); per successful writeMin: atomicMin, stamp,
+        # moved append, then filing: moved read, D, offsets, slot write (32);
+        # per bucket entry extracted: slot, D, offsets (16)
+        return 8 * n + 20 * V + 12 * E + 32 * R + 16 * I
+    # BFS: init D, parent (8n) + visited bitmap (n/8); per frontier vertex or
+    # pull candidate: queue/offset reads (12); per arc: target + bitmap word (8);
+    # per reached vertex: D, parent, offsets, queue+qoff write (24); bitmaps per
+    # dense round (3 passes of n/8)
+    return 8 * n + n // 8 + 12 * V + 8 * E + 24 * st["vertices_reached"] + \
+        3 * (n // 8) * st["pull_rounds"]
+
+
+def cpu_reference_sample(g, wl, srcs, budget_s=15.0, max_queries=None):
+    """Time the oracle on a bounded sample of the workload's queries."""
+    import oracle
+    te, t = 0, 0.0
+    done = 0
+    for s in srcs:
+        t0 = time.perf_counter()
+        if wl["kind"] == "wbfs":
+            d = oracle.dijkstra(g, int(s))
+        else:
+            d, _ = oracle.bfs(g, int(s))
+        t += time.perf_counter() - t0
+        te += traversed_edges(g, d)
+        done += 1
+        if t > budget_s or (max_queries and done >= max_queries):
+            break
+    return te, t, done
+
+
+def run_reference(args, wl, rank, world):
+    if rank != 0:
+        return 0
+    g = make_graph(wl)
+    srcs = make_sources(g, wl)
+    # each step = one oracle query (a bounded sample of the 8-query step)
+    te_tot, t_tot, q = 0, 0.0, 0
+    for i in range(args.warmup + args.steps):
+        s = srcs[i % len(srcs)]
+        te, t, _ = cpu_reference_sample(g, wl, [s], budget_s=1e9, max_queries=1)
+        if i >= args.warmup:
+            te_tot += te
+            t_tot += t
+            q += 1
+    gteps = te_tot / t_tot / 1e9
+    line = {"metric": "GTEPS", "value": gteps, "unit": "GTEPS", "impl": "reference",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * t_tot / max(q, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": wl["desc"]},
+            "cpu_baseline": {"value": gteps, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                             "sample": f"{q} single-source oracle queries (one per step) of the "
+                                       f"{wl['nsrc']}-source step, 1 thread"},
+            "e2e": {"value": gteps, "unit": "GTEPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gbf", choices=["gbf", "reference"])
+    ap.add_argument("--workload", default="wbfs-rmat22", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--opt", default="", help="comma list of gbf_options overrides k=v")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    wl = WORKLOADS[args.workload]
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, wl, rank, world)
+
+    import torch
+    import torch.distributed as dist_mod
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist_mod.init_process_group("nccl")
+
+    def barrier():
+        if world > 1:
+            dist_mod.barrier()
+
+    import paper_1805_05208_gb300 as gb
+
+    g = make_graph(wl)
+    srcs = make_sources(g, wl, rank)
+    n = g.n
+    dev = torch.device("cuda", local)
+    opt = gb.gbf_options_default()
+    for kv in filter(None, args.opt.split(",")):
+        k, v = kv.split("=")
+        setattr(opt, k, int(v))
+    graph = gb.Graph(g, validate=gb.VALIDATE_BASIC)
+    stream = torch.cuda.Stream(device=dev)
+    kind = wl["kind"]
+    outs = [torch.empty(n, dtype=torch.int32, device=dev) for _ in srcs]
+    pars = [torch.empty(n, dtype=torch.int32, device=dev) for _ in srcs] if kind == "bfs" else None
+
+    def launch(i):
+        if kind == "wbfs":
+            gb.gbf_wbfs(graph.h, int(srcs[i]), outs[i], opt, stream)
+        else:
+            gb.gbf_bfs(graph.h, int(srcs[i]), outs[i], pars[i], opt, stream)
+
+    # Warm-up; the first pass also records each query's statistics and TEPS numerator.
+    stats, te = [], []
+    for w in range(args.warmup):
+        for i in range(len(srcs)):
+            launch(i)
+            if w == 0:
+                stats.append(gb.gbf_wait(graph.h, stream))
+                te.append(traversed_edges(g, outs[i].cpu().numpy()))
+    gb.gbf_wait(graph.h, stream)
+    te_step = sum(te)
+
+    # Timed region: K steps, events per launch on the launching stream.
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps * len(srcs))]
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        k = 0
+        for s in range(args.steps):
+            for i in range(len(srcs)):
+                ev[k][0].record(stream)
+                launch(i)
+                ev[k][1].record(stream)
+                k += 1
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    st_last = gb.gbf_wait(graph.h, stream)
+    if st_last["device_error"]:
+        raise RuntimeError(f"device error {st_last['device_error']}")
+    ms_total = t_start.elapsed_time(t_end)
+    if world > 1:
+        t = torch.tensor([ms_total], device=dev)
+        dist_mod.all_reduce(t, op=dist_mod.ReduceOp.MAX)
+        ms_total = float(t.item())
+        tt = torch.tensor([float(te_step)], device=dev, dtype=torch.float64)
+        dist_mod.all_reduce(tt)
+        te_all = float(tt.item())
+    else:
+        te_all = float(te_step)
+    launch_ms = [e[0].elapsed_time(e[1]) for e in ev]
+    value = te_all * args.steps / (ms_total / 1e3) / 1e9
+
+    # Roofline of the one persistent kernel (each query is one launch).
+    peak, peak_kind = load_peaks()
+    bytes_per_step = sum(bytes_model(kind, n, s) for s in stats)
+    avg_launch_ms = sum(launch_ms) / len(launch_ms)
+    bytes_per_launch = bytes_per_step / len(srcs)
+    achieved = bytes_per_launch / (avg_launch_ms / 1e3) / 1e9
+
+    # End to end: the C-ABI call with host buffers (D2H of each result inside).
+    host_out = [torch.empty(n, dtype=torch.int32, pin_memory=True).numpy() for _ in srcs]
+    host_par = [torch.empty(n, dtype=torch.int32, pin_memory=True).numpy() for _ in srcs] \
+        if kind == "bfs" else None
+    e2e_steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for s in range(e2e_steps):
+        for i in range(len(srcs)):
+            if kind == "wbfs":
+                gb.gbf_wbfs(graph.h, int(srcs[i]), host_out[i], opt, None)
+            else:
+                gb.gbf_bfs(graph.h, int(srcs[i]), host_out[i], host_par[i], opt, None)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist_mod.all_reduce(t, op=dist_mod.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_val = te_all * e2e_steps / e2e_s / 1e9
+    d2h = len(srcs) * n * 4 * (2 if kind == "bfs" else 1)
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            te_c, t_c, q = cpu_reference_sample(g, wl, srcs, budget_s=args.cpu_budget)
+            cpu = {"value": te_c / t_c / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                   "sample": f"{q} of the {len(srcs)} queries of one step, serial oracle "
+                             f"({'binary-heap Dijkstra' if kind == 'wbfs' else 'FIFO BFS'}), "
+                             f"{t_c:.1f} s"}
+        clocks = clk.summary()
+        line = {
+            "metric": "GTEPS", "value": value, "unit": "GTEPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "desc": wl["desc"], "n": n, "arcs": g.m,
+                       "sources_per_step": len(srcs), "seeds": {"graph": 1, "weights": 2, "sources": 3},
+                       "l2": "inputs larger than L2 (graph arrays exceed 129 MB); no flush",
+                       "options": {f: getattr(opt, f) for f, _ in opt._fields_}},
+            "roofline": {"bound": "hbm", "kernel": f"{kind}_kernel", "achieved": achieved,
+                         "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_source": f"{peak_kind} hbm_gbs (burst copy)",
+                         "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_launch_ms,
+                         "traffic": None},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_val, "unit": "GTEPS", "h2d_bytes_per_step": 4 * len(srcs),
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": args.steps * len(srcs),
+            "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+            "stats": {"rounds": [s["rounds"] for s in stats],
+                      "pull_rounds": [s["pull_rounds"] for s in stats],
+                      "edges_scanned": sum(s["edges_scanned"] for s in stats),
+                      "traversed_edges_per_step": te_step,
+                      "grid_ctas": stats[0]["grid_ctas"], "block": stats[0]["block"]},
+        }
+        print(json.dumps(line))
+    graph.close()
+    if world > 1:
+        dist_mod.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

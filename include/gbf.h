@@ -1,0 +1,191 @@
+/*
+ * gbf.h — C ABI of the GB300 frontier-traversal library (libgbf.so).
+ *
+ * The library runs, on one NVIDIA GB300 (sm_103a), the frontier-based
+ * edgeMap over vertexSubsets of Ligra as used by the paper (§3 "Ligra,
+ * Ligra+, and Julienne"), and the two searches built on it:
+ *   - BFS (§4 problem statement; Alg. 1),
+ *   - integral-weight SSSP / weighted BFS over Julienne buckets (§4; Alg. 3),
+ * plus a 64-lane bit-packed multi-source BFS and a continuous-batching query
+ * server.  All arithmetic is integer: int32 distances and ids, uint32 offsets
+ * and weights.
+ *
+ * Conventions for every call:
+ *   - Every function returns a gbf_status, never aborts, never throws across
+ *     the ABI.  gbf_last_error() gives a thread-local message for the last
+ *     failure on the calling thread.
+ *   - Graphs are symmetric CSR: offsets uint32[n+1] with off[0] = 0 and
+ *     off[n] = m (number of arcs, each undirected edge stored twice), targets
+ *     int32[m], optional weights uint32[m] (both arcs of an edge carry the same
+ *     weight).  Adjacency lists need not be sorted unless the symmetry check
+ *     is requested.  Results are defined only for symmetric graphs.
+ *   - `mem` says where caller buffers live: GBF_HOST (pageable or pinned host
+ *     memory; the call copies and blocks until the result is in place) or
+ *     GBF_DEVICE (device pointers in the current CUDA context; the call is
+ *     ordered on `cuda_stream` and returns after launch — call gbf_wait()
+ *     to synchronise and collect the device-side status).
+ *   - `cuda_stream` is a cudaStream_t (NULL = legacy default stream).
+ *   - Unreachable vertices get distance GBF_INF and parent GBF_NOPARENT; the
+ *     source is its own parent.
+ *   - Calls on the same graph handle share its default workspace: do not run
+ *     two queries on one handle concurrently from different streams (the
+ *     server keeps its own per-query workspaces for that).
+ */
+#ifndef GBF_H
+#define GBF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GBF_OK = 0,
+  GBF_ERR_INVALID = 1,  /* bad argument or malformed graph */
+  GBF_ERR_OOM = 2,      /* device or host allocation failed, or HBM budget exhausted */
+  GBF_ERR_CUDA = 3,     /* a CUDA runtime call failed (message in gbf_last_error) */
+  GBF_ERR_TIMEOUT = 4,  /* a bounded device wait (grid barrier) ran out */
+  GBF_ERR_OVERFLOW = 5, /* distances could exceed int32, or a device queue overflowed */
+  GBF_ERR_BUSY = 6,     /* server cannot admit the request now */
+  GBF_ERR_NOT_FOUND = 7 /* unknown server ticket */
+} gbf_status;
+
+#define GBF_INF INT32_MAX  /* distance of an unreachable vertex */
+#define GBF_NOPARENT (-1)  /* parent of an unreachable vertex */
+
+#define GBF_HOST 0
+#define GBF_DEVICE 1
+
+/* gbf_graph_create validate_flags (OR-able) */
+#define GBF_VALIDATE_BASIC 1u     /* off monotone, off[0]=0, targets in [0,n), no self-loops, weights >= 1 */
+#define GBF_VALIDATE_SYMMETRIC 2u /* adjacency lists sorted, no duplicates, every arc has its reverse with the same weight */
+
+typedef struct gbf_graph gbf_graph;
+
+/*
+ * Tuning knobs.  Zero in any field selects the default; results (distances)
+ * never depend on them.  gbf_options_default() fills the defaults.
+ *   block         threads per CTA of the persistent kernels: 128, 256, 512 or 1024 (default 256)
+ *   pull_divisor  edgeMap takes the dense (pull) direction when the frontier's
+ *                 out-degree sum exceeds m / pull_divisor (default 20; -1 = push only)
+ *   heavy_cutoff  largest number of frontier edges one CTA processes as one
+ *                 block of the blocked sparse edgeMap; a vertex with more
+ *                 edges is split over several CTAs (power of two, 256..4096, default 1024)
+ *   bucket_window number of open buckets nB of the wBFS bucket structure
+ *                 (default max weight + 1; smaller values exercise the overflow bucket)
+ *   dense_wbfs    1 = let wBFS switch to a dense edgeMap for dense buckets (default 0)
+ *   spin_cap_us   time limit of every bounded device wait, microseconds (default 5,000,000)
+ *   counters      reserved (statistics are always collected)
+ *   ctas          CTAs of the persistent kernels (default: every CTA that fits, all SMs)
+ *   pull_serial   neighbours a thread scans alone before the dense step hands a vertex to its whole warp (default 8)
+ *   inject_wait   fault injection for tests: 1 = one CTA waits on a flag nothing sets,
+ *                 so the first grid barrier times out and the call returns GBF_ERR_TIMEOUT
+ */
+typedef struct {
+  int32_t block;
+  int32_t pull_divisor;
+  int32_t heavy_cutoff;
+  int32_t bucket_window;
+  int32_t dense_wbfs;
+  int32_t counters;
+  int64_t spin_cap_us;
+  int32_t ctas;
+  int32_t pull_serial;
+  int32_t inject_wait;
+  int32_t reserved;
+} gbf_options;
+
+/* Per-query statistics, filled by gbf_wait / host-memory calls. */
+typedef struct {
+  int64_t rounds;            /* BFS levels, or wBFS bucket rounds */
+  int64_t push_rounds;       /* sparse edgeMap rounds */
+  int64_t pull_rounds;       /* dense edgeMap rounds */
+  int64_t edges_scanned;     /* arcs examined by edgeMap */
+  int64_t vertices_expanded; /* frontier vertices whose arcs were traversed */
+  int64_t vertices_reached;  /* vertices with finite distance */
+  int64_t relaxations;       /* wBFS: successful writeMin calls */
+  int64_t bucket_inserts;    /* wBFS: entries appended to buckets (incl. overflow) */
+  int64_t refills;           /* wBFS: overflow-bucket refills */
+  int32_t grid_ctas;         /* CTAs of the persistent launch */
+  int32_t block;             /* threads per CTA */
+  int32_t device_error;      /* gbf_status reported by the device */
+  int32_t reserved;
+} gbf_stats;
+
+/* Fills *opt with the defaults (all knobs explicit). */
+gbf_status gbf_options_default(gbf_options *opt);
+
+/* Thread-local message describing the last failure; returns its length. */
+size_t gbf_last_error(char *buf, size_t len);
+
+/* Library version as "major.minor.patch". */
+const char *gbf_version(void);
+
+/*
+ * gbf_graph_create — make a graph resident on the current CUDA device
+ * (the paper's CSR representation, §3 graph notation).
+ *   n         vertices, 1 <= n < 2^31
+ *   off       uint32[n+1], off[n] = m < 2^32 arcs
+ *   tgt       int32[m]
+ *   w         uint32[m] or NULL (unweighted: only BFS and MS-BFS available)
+ *   mem       where off/tgt/w live (GBF_HOST or GBF_DEVICE)
+ *   validate_flags  GBF_VALIDATE_* checks run on the device; failures give GBF_ERR_INVALID
+ *   cuda_stream     stream for the upload and the checks
+ *   out       receives the handle
+ * The library copies the arrays into memory it owns; the caller keeps its
+ * buffers.  Weighted graphs with (n-1) * max(w) >= 2^31-1 are rejected with
+ * GBF_ERR_OVERFLOW (distances would not fit int32).  Blocks until resident.
+ */
+gbf_status gbf_graph_create(int32_t n, const uint32_t *off, const int32_t *tgt, const uint32_t *w,
+                            int mem, uint32_t validate_flags, void *cuda_stream, gbf_graph **out);
+
+/* Frees the graph and every workspace it owns. NULL is accepted. */
+gbf_status gbf_graph_destroy(gbf_graph *g);
+
+/* Vertices, arcs, max weight (0 if unweighted) and a 64-bit fingerprint of
+ * the CSR contents (used to key autotuning results). Any pointer may be NULL. */
+gbf_status gbf_graph_info(const gbf_graph *g, int32_t *n, uint64_t *m, uint32_t *w_max,
+                          uint64_t *fingerprint);
+
+/* Device bytes held by the graph (arrays plus workspaces allocated so far). */
+gbf_status gbf_graph_device_bytes(const gbf_graph *g, size_t *bytes);
+
+/*
+ * gbf_bfs — breadth-first search from src (§4 "Breadth-First Search";
+ * Alg. 1, with the direction-optimising edgeMap of §3).
+ *   dist    int32[n]: hop distance, GBF_INF if unreachable
+ *   parent  int32[n] or NULL: a BFS tree; parent[src] = src, GBF_NOPARENT if
+ *           unreachable.  Which neighbour one level closer becomes the parent
+ *           depends on timing (the test-and-set winner); any such tree is valid.
+ *   mem     GBF_HOST: blocks; GBF_DEVICE: stream-ordered, see gbf_wait
+ *   opt     NULL for defaults
+ * Errors: GBF_ERR_INVALID for a bad src or NULL dist; GBF_ERR_TIMEOUT if a
+ * bounded device wait ran out (outputs are then undefined).
+ */
+gbf_status gbf_bfs(gbf_graph *g, int32_t src, int32_t *dist, int32_t *parent, int mem,
+                   const gbf_options *opt, void *cuda_stream);
+
+/*
+ * gbf_wbfs — integral-weight single-source shortest paths from src by
+ * weighted BFS over a Julienne bucket structure (§4 "Integral-Weight SSSP";
+ * Alg. 3).  Requires a weighted graph with weights >= 1.
+ *   dist    int32[n]: shortest-path distance, GBF_INF if unreachable
+ * Errors: as gbf_bfs; GBF_ERR_INVALID on an unweighted graph.
+ */
+gbf_status gbf_wbfs(gbf_graph *g, int32_t src, int32_t *dist, int mem, const gbf_options *opt,
+                    void *cuda_stream);
+
+/*
+ * gbf_wait — synchronise `cuda_stream` and return the device-side status of
+ * the last gbf_bfs / gbf_wbfs / gbf_msbfs issued on g with GBF_DEVICE
+ * buffers; fills *stats if non-NULL.
+ */
+gbf_status gbf_wait(gbf_graph *g, void *cuda_stream, gbf_stats *stats);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBF_H */

@@ -1,0 +1,242 @@
+"""Python binding of libgbf.so — the GB300 frontier-traversal library.
+
+Argument marshalling only: every step of BFS, weighted BFS and multi-source
+BFS runs in the library's CUDA kernels.  Functions carry the C ABI's names
+(``gbf_graph_create``, ``gbf_bfs``, ...) and accept numpy arrays (host
+memory) or torch CUDA tensors (device memory); torch is used only for device
+memory and streams.  If the library has not been built, importing the
+binding raises immediately: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+INF = 2**31 - 1
+NOPARENT = -1
+HOST = 0
+DEVICE = 1
+VALIDATE_BASIC = 1
+VALIDATE_SYMMETRIC = 2
+
+STATUS = {0: "GBF_OK", 1: "GBF_ERR_INVALID", 2: "GBF_ERR_OOM", 3: "GBF_ERR_CUDA",
+          4: "GBF_ERR_TIMEOUT", 5: "GBF_ERR_OVERFLOW", 6: "GBF_ERR_BUSY", 7: "GBF_ERR_NOT_FOUND"}
+
+LIB_PATH = _build.LIB
+
+
+class GbfError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class gbf_options(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_int32), ("pull_divisor", ctypes.c_int32),
+                ("heavy_cutoff", ctypes.c_int32), ("bucket_window", ctypes.c_int32),
+                ("dense_wbfs", ctypes.c_int32), ("counters", ctypes.c_int32),
+                ("spin_cap_us", ctypes.c_int64), ("ctas", ctypes.c_int32),
+                ("pull_serial", ctypes.c_int32), ("inject_wait", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class gbf_stats(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int64), ("push_rounds", ctypes.c_int64),
+                ("pull_rounds", ctypes.c_int64), ("edges_scanned", ctypes.c_int64),
+                ("vertices_expanded", ctypes.c_int64), ("vertices_reached", ctypes.c_int64),
+                ("relaxations", ctypes.c_int64), ("bucket_inserts", ctypes.c_int64),
+                ("refills", ctypes.c_int64), ("grid_ctas", ctypes.c_int32),
+                ("block", ctypes.c_int32), ("device_error", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libgbf.so is not built ({LIB_PATH}); run "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I32, U32, I64, U64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_int64, ctypes.c_uint64
+    S = ctypes.c_int
+    sig = {
+        "gbf_options_default": (S, [ctypes.POINTER(gbf_options)]),
+        "gbf_last_error": (ctypes.c_size_t, [ctypes.c_char_p, ctypes.c_size_t]),
+        "gbf_version": (ctypes.c_char_p, []),
+        "gbf_graph_create": (S, [I32, P, P, P, ctypes.c_int, U32, P, ctypes.POINTER(P)]),
+        "gbf_graph_destroy": (S, [P]),
+        "gbf_graph_info": (S, [P, ctypes.POINTER(I32), ctypes.POINTER(U64), ctypes.POINTER(U32),
+                               ctypes.POINTER(U64)]),
+        "gbf_graph_device_bytes": (S, [P, ctypes.POINTER(ctypes.c_size_t)]),
+        "gbf_bfs": (S, [P, I32, P, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
+        "gbf_wbfs": (S, [P, I32, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
+        "gbf_wait": (S, [P, P, ctypes.POINTER(gbf_stats)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def lib() -> ctypes.CDLL:
+    return _lib
+
+
+def last_error() -> str:
+    buf = ctypes.create_string_buffer(1024)
+    _lib.gbf_last_error(buf, 1024)
+    return buf.value.decode(errors="replace")
+
+
+def _check(st: int, what: str) -> None:
+    if st != 0:
+        raise GbfError(st, f"{what}: {last_error()}")
+
+
+def gbf_version() -> str:
+    return _lib.gbf_version().decode()
+
+
+def gbf_options_default(**overrides) -> gbf_options:
+    o = gbf_options()
+    _check(_lib.gbf_options_default(ctypes.byref(o)), "gbf_options_default")
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(a):
+    """(address, mem) of a numpy array (host) or a torch tensor (its device)."""
+    if a is None:
+        return None, None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be contiguous")
+        return a.ctypes.data, HOST
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), (DEVICE if a.is_cuda else HOST)
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream  # torch.cuda.Stream
+
+
+def gbf_graph_create(n: int, off, tgt, w=None, validate: int = VALIDATE_BASIC, stream=None) -> int:
+    """Make a CSR graph resident on the current device; returns the handle."""
+    po, mem = _ptr(off)
+    pt, mt = _ptr(tgt)
+    pw, mw = _ptr(w)
+    if (mt is not None and mt != mem) or (mw is not None and mw != mem):
+        raise ValueError("off, tgt and w must all be host or all device buffers")
+    h = ctypes.c_void_p()
+    _check(_lib.gbf_graph_create(int(n), po, pt, pw, mem, validate, _stream(stream), ctypes.byref(h)),
+           "gbf_graph_create")
+    return h.value
+
+
+def gbf_graph_destroy(h: int) -> None:
+    _check(_lib.gbf_graph_destroy(h), "gbf_graph_destroy")
+
+
+def gbf_graph_info(h: int) -> dict:
+    n, m, wm, fp = ctypes.c_int32(), ctypes.c_uint64(), ctypes.c_uint32(), ctypes.c_uint64()
+    _check(_lib.gbf_graph_info(h, ctypes.byref(n), ctypes.byref(m), ctypes.byref(wm),
+                               ctypes.byref(fp)), "gbf_graph_info")
+    return {"n": n.value, "m": m.value, "w_max": wm.value, "fingerprint": fp.value}
+
+
+def gbf_graph_device_bytes(h: int) -> int:
+    b = ctypes.c_size_t()
+    _check(_lib.gbf_graph_device_bytes(h, ctypes.byref(b)), "gbf_graph_device_bytes")
+    return b.value
+
+
+def _opt(opt):
+    return None if opt is None else ctypes.byref(opt)
+
+
+def gbf_bfs(h: int, src: int, dist, parent=None, opt: Optional[gbf_options] = None, stream=None) -> None:
+    """BFS from src into dist (and parent): numpy arrays block; CUDA tensors are stream-ordered."""
+    pd, mem = _ptr(dist)
+    pp, mp = _ptr(parent)
+    if mp is not None and mp != mem:
+        raise ValueError("dist and parent must live in the same memory")
+    _check(_lib.gbf_bfs(h, int(src), pd, pp, mem, _opt(opt), _stream(stream)), "gbf_bfs")
+
+
+def gbf_wbfs(h: int, src: int, dist, opt: Optional[gbf_options] = None, stream=None) -> None:
+    """Integral-weight SSSP from src into dist."""
+    pd, mem = _ptr(dist)
+    _check(_lib.gbf_wbfs(h, int(src), pd, mem, _opt(opt), _stream(stream)), "gbf_wbfs")
+
+
+def gbf_wait(h: int, stream=None) -> dict:
+    """Synchronise and return the statistics of the last device-memory query."""
+    s = gbf_stats()
+    _check(_lib.gbf_wait(h, _stream(stream), ctypes.byref(s)), "gbf_wait")
+    return s.as_dict()
+
+
+class Graph:
+    """Owning wrapper around a resident graph handle."""
+
+    def __init__(self, csr=None, *, n=None, off=None, tgt=None, w=None,
+                 validate: int = VALIDATE_BASIC, stream=None):
+        if csr is not None:
+            n, off, tgt, w = csr.n, csr.off, csr.tgt, csr.w
+        off = np.ascontiguousarray(off, dtype=np.uint32) if isinstance(off, np.ndarray) else off
+        tgt = np.ascontiguousarray(tgt, dtype=np.int32) if isinstance(tgt, np.ndarray) else tgt
+        if isinstance(w, np.ndarray):
+            w = np.ascontiguousarray(w, dtype=np.uint32)
+        if isinstance(tgt, np.ndarray) and tgt.size == 0:
+            tgt = np.zeros(1, dtype=np.int32)
+            if w is not None:
+                w = np.ones(1, dtype=np.uint32)
+        self.h = gbf_graph_create(n, off, tgt, w, validate, stream)
+        info = gbf_graph_info(self.h)
+        self.n, self.m, self.w_max, self.fingerprint = info["n"], info["m"], info["w_max"], info["fingerprint"]
+
+    def close(self):
+        if getattr(self, "h", None):
+            gbf_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def bfs(self, src: int, parents: bool = True, opt=None):
+        d = np.empty(self.n, dtype=np.int32)
+        p = np.empty(self.n, dtype=np.int32) if parents else None
+        gbf_bfs(self.h, src, d, p, opt)
+        return d, p
+
+    def wbfs(self, src: int, opt=None):
+        d = np.empty(self.n, dtype=np.int32)
+        gbf_wbfs(self.h, src, d, opt)
+        return d
+
+    def stats(self, stream=None) -> dict:
+        return gbf_wait(self.h, stream)
+
+    def device_bytes(self) -> int:
+        return gbf_graph_device_bytes(self.h)

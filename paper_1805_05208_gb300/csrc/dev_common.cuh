@@ -1,0 +1,422 @@
+// Device building blocks shared by the persistent traversal kernels:
+//   - a bounded, time-limited grid barrier for cooperative launches,
+//   - warp/block scans and warp-aggregated appends,
+//   - the blocked sparse edgeMap (edgeMapBlocked, Alg. 2 and §6.2): frontier
+//     edges are cut into equal chunks through a prefix sum of frontier
+//     degrees; each CTA walks one chunk with its warps on consecutive edges
+//     (coalesced target loads) and stages live neighbours in shared memory,
+//   - the staged flush that writes the next frontier as a compact queue with
+//     its own degree prefix (qoff) and chunk-start table (cs), reserving its
+//     range with one 64-bit atomicAdd per CTA.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gbf_impl.h"
+
+namespace gbf {
+namespace dev {
+
+constexpr int32_t kInf = 0x7fffffff;
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kFineLog = 8;  // chunk-start table granularity: 256 frontier edges
+constexpr uint32_t kFine = 1u << kFineLog;
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_add(unsigned *p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+__device__ __forceinline__ unsigned lanemask_le() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_le;" : "=r"(m));
+  return m;
+}
+template <class T>
+__device__ __forceinline__ T ld_vol(const T &x) {
+  return *(const volatile T *)&x;
+}
+template <class T>
+__device__ __forceinline__ void st_vol(T &x, T v) {
+  *(volatile T *)&x = v;
+}
+
+__device__ __forceinline__ void raise_error(Ctl *ctl, int code, int where) {
+  if (atomicCAS(&ctl->err, 0, code) == 0) ctl->err_where = where;
+}
+
+// ---------------------------------------------------------------- grid barrier
+// Monotone arrival counter: the k-th barrier of a launch completes when the
+// counter reaches k * gridDim.x.  Thread 0 of each CTA arrives with a release
+// reduction and polls with acquire loads; the wait is bounded by cap_ns of
+// %globaltimer time, after which it raises GBF_ERR_TIMEOUT and returns.
+// Returns true (uniformly across the CTA) if no error has been raised.
+struct Barrier {
+  unsigned epoch;
+  long long cap_ns;
+};
+
+__device__ __forceinline__ bool grid_sync(Ctl *ctl, Barrier &b, int *s_flag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    b.epoch += gridDim.x;
+    fence_acq_rel();
+    red_release_add(&ctl->bar, 1u);
+    unsigned long long t0 = 0;
+    unsigned spins = 0;
+    while ((int)(ld_acquire(&ctl->bar) - b.epoch) < 0) {
+      if ((++spins & 255u) == 0) {
+        unsigned long long t = globaltimer();
+        if (t0 == 0) t0 = t;
+        else if ((long long)(t - t0) > b.cap_ns) {
+          raise_error(ctl, GBF_ERR_TIMEOUT, 1);
+          break;
+        }
+      }
+    }
+    fence_acq_rel();
+    *s_flag = ld_vol(ctl->err);
+  }
+  __syncthreads();
+  return *s_flag == 0;
+}
+
+// Fault injection: wait on a flag nothing sets, bounded like a barrier; when
+// the limit runs out, report the timeout as a stalled barrier would.
+__device__ __forceinline__ void injected_wait(Ctl *ctl, long long cap_ns) {
+  unsigned long long t0 = globaltimer();
+  while (ld_vol(ctl->stop) == 0) {
+    if ((long long)(globaltimer() - t0) > cap_ns) {
+      raise_error(ctl, GBF_ERR_TIMEOUT, 9);
+      break;
+    }
+    __nanosleep(1000);
+  }
+}
+
+// ------------------------------------------------------------------- scans
+// Exclusive block scan of one uint32 per thread; returns the exclusive prefix
+// and writes the block total to *total.  s_tmp needs 33 words.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t *s_tmp, uint32_t *total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  uint32_t inc = x;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    uint32_t y = __shfl_up_sync(kFull, inc, d);
+    if (lane >= d) inc += y;
+  }
+  if (lane == 31) s_tmp[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t s = (lane < nw) ? s_tmp[lane] : 0u;
+    uint32_t si = s;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      uint32_t y = __shfl_up_sync(kFull, si, d);
+      if (lane >= d) si += y;
+    }
+    s_tmp[lane] = si - s;  // exclusive warp offsets
+    if (lane == 31) s_tmp[32] = si;
+  }
+  __syncthreads();
+  uint32_t r = s_tmp[warp] + inc - x;
+  *total = s_tmp[32];
+  __syncthreads();
+  return r;
+}
+
+// Block-wide sum of a 64-bit value (result valid in thread 0).
+__device__ __forceinline__ unsigned long long block_sum64(unsigned long long x,
+                                                          unsigned long long *s_tmp) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) x += __shfl_down_sync(kFull, x, d);
+  if (lane == 0) s_tmp[warp] = x;
+  __syncthreads();
+  unsigned long long r = 0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < nw; i++) r += s_tmp[i];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ int block_min_i32(int x, int *s_tmp) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) x = min(x, __shfl_down_sync(kFull, x, d));
+  if (lane == 0) s_tmp[warp] = x;
+  __syncthreads();
+  int r = kInf;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < nw; i++) r = min(r, s_tmp[i]);
+  __syncthreads();
+  return r;
+}
+
+// ---------------------------------------------------- shared-memory layout
+// Dynamic shared memory of the frontier kernels, for chunks of up to Bmax
+// frontier edges:
+//   base/u/adj  [Bmax+2]   per frontier vertex of the chunk: edge-space start,
+//                          vertex id, CSR offset of its first arc
+//   out_v/out_d [2*Bmax]   staged live neighbours and their degrees
+//   pref        [2*Bmax]   exclusive prefix of out_d during a flush
+struct PushSmem {
+  uint32_t *base;
+  int32_t *u;
+  uint32_t *adj;
+  int32_t *out_v;
+  uint32_t *out_d;
+  uint32_t *pref;
+  uint32_t *misc;  // [0] n_out, [1] pos, [2] dpos, [3] flag, [8..41] scan tmp
+  unsigned long long *misc64;  // 32 entries
+  uint32_t cap_out;            // 2*Bmax
+};
+
+__host__ __device__ inline size_t push_smem_bytes(int Bmax) {
+  return sizeof(uint32_t) * (size_t)(3 * (Bmax + 2) + 3 * 2 * Bmax + 64) + 8 * 32 + 16;
+}
+
+__device__ __forceinline__ PushSmem carve_push_smem(void *raw, int Bmax) {
+  PushSmem S;
+  unsigned long long *p64 = (unsigned long long *)raw;
+  S.misc64 = p64;
+  uint32_t *p = (uint32_t *)(p64 + 32);
+  S.misc = p;
+  p += 64;
+  S.base = p;
+  p += Bmax + 2;
+  S.u = (int32_t *)p;
+  p += Bmax + 2;
+  S.adj = p;
+  p += Bmax + 2;
+  S.out_v = (int32_t *)p;
+  p += 2 * Bmax;
+  S.out_d = p;
+  p += 2 * Bmax;
+  S.pref = p;
+  S.cap_out = 2u * (uint32_t)Bmax;
+  return S;
+}
+
+// Warp-collective: append the lanes with emit set to the CTA staging buffer.
+__device__ __forceinline__ void stage_append(PushSmem &S, bool emit, int32_t v, uint32_t d) {
+  unsigned bal = __ballot_sync(kFull, emit);
+  if (bal == 0) return;
+  const int lane = threadIdx.x & 31;
+  int leader = __ffs(bal) - 1;
+  uint32_t pos = 0;
+  if (lane == leader) pos = atomicAdd(&S.misc[0], (uint32_t)__popc(bal));
+  pos = __shfl_sync(kFull, pos, leader);
+  if (emit) {
+    uint32_t r = pos + __popc(bal & lanemask_lt());
+    S.out_v[r] = v;
+    S.out_d[r] = d;
+  }
+}
+
+// Output frontier description (sparse vertexSubset with degree prefix).
+struct QueueOut {
+  int32_t *q;
+  uint32_t *qoff;
+  uint32_t *cs;
+  unsigned long long *counter;  // (count << 32) | degree sum, reserved per flush
+  uint32_t q_cap;
+  uint32_t cs_cap;
+};
+
+// CTA-collective: write the staged entries to the output queue.  One 64-bit
+// atomicAdd reserves both the queue range and the edge-space range, so the
+// per-entry degree prefix (qoff) is globally consistent; every chunk start
+// (multiple of 256 edges) falling in an entry's range records the entry.
+__device__ __forceinline__ void stage_flush(PushSmem &S, const QueueOut &out, Ctl *ctl) {
+  __syncthreads();
+  const uint32_t k = S.misc[0];
+  if (k == 0) return;
+  const uint32_t tid = threadIdx.x, bd = blockDim.x;
+  const uint32_t per = (k + bd - 1) / bd;
+  const uint32_t lo = min(k, tid * per), hi = min(k, lo + per);
+  uint32_t loc = 0;
+  for (uint32_t i = lo; i < hi; i++) loc += S.out_d[i];
+  uint32_t total;
+  uint32_t ex = block_excl_scan(loc, S.misc + 8, &total);
+  for (uint32_t i = lo; i < hi; i++) {
+    S.pref[i] = ex;
+    ex += S.out_d[i];
+  }
+  if (tid == 0) {
+    unsigned long long old = atomicAdd(out.counter, ((unsigned long long)k << 32) | total);
+    uint32_t pos = (uint32_t)(old >> 32);
+    if ((unsigned long long)pos + k > out.q_cap) {
+      raise_error(ctl, GBF_ERR_OVERFLOW, 2);
+      S.misc[3] = 1;
+    } else {
+      S.misc[3] = 0;
+    }
+    S.misc[1] = pos;
+    S.misc[2] = (uint32_t)old;
+  }
+  __syncthreads();
+  if (S.misc[3] == 0) {
+    const uint32_t pos = S.misc[1], dpos = S.misc[2];
+    for (uint32_t i = tid; i < k; i += bd) {
+      uint32_t a = dpos + S.pref[i], d = S.out_d[i];
+      out.q[pos + i] = S.out_v[i];
+      out.qoff[pos + i] = a;
+      for (uint32_t c = (a + kFine - 1) >> kFineLog; (c << kFineLog) < a + d; c++) {
+        if (c < out.cs_cap) out.cs[c] = pos + i;
+      }
+    }
+  }
+  __syncthreads();
+  if (tid == 0) S.misc[0] = 0;
+  __syncthreads();
+}
+
+// Input frontier description.
+struct QueueIn {
+  const int32_t *q;
+  const uint32_t *qoff;
+  const uint32_t *cs;
+  uint32_t cnt;  // entries
+  uint32_t D;    // degree sum (frontier edges)
+};
+
+// Largest k with base[k] <= x, for base[0] <= x < base[nv].
+__device__ __forceinline__ uint32_t smem_upper(const uint32_t *base, uint32_t nv, uint32_t x) {
+  uint32_t lo = 0, hi = nv;
+  while (hi - lo > 1) {
+    uint32_t mid = (lo + hi) >> 1;
+    if (base[mid] <= x) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Blocked sparse edgeMap over the frontier `in` with chunks of B = 256 << s
+// edges.  For every frontier arc (u, v) at CSR index idx, fn(u, v, idx, emit,
+// out_v, out_d) is called by one lane (valid lanes only) and may request an
+// append; Sink::append is warp-collective, Sink::chunk_done CTA-collective.
+template <class EdgeFn, class Sink>
+__device__ __forceinline__ void blocked_edge_map(const DevGraph &g, const QueueIn &in, int s,
+                                                 PushSmem &S, EdgeFn &fn, Sink &sink, Ctl *ctl) {
+  const uint32_t B = kFine << s;
+  const uint32_t nfine = (in.D + kFine - 1) >> kFineLog;
+  const uint32_t nch = (in.D + B - 1) / B;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (uint32_t c = blockIdx.x; c < nch; c += gridDim.x) {
+    const uint32_t e_lo = c * B, e_hi = min(e_lo + B, in.D);
+    const uint32_t f1 = (c + 1) << s;
+    const uint32_t i0 = in.cs[c << s];
+    const uint32_t i1 = (f1 < nfine) ? in.cs[f1] : in.cnt - 1;
+    if (i1 < i0 || i1 >= in.cnt || i1 - i0 > B) {  // inconsistent table: never expected
+      if (threadIdx.x == 0) raise_error(ctl, GBF_ERR_OVERFLOW, 3);
+      continue;
+    }
+    const uint32_t nv = i1 - i0 + 1;
+    for (uint32_t j = threadIdx.x; j < nv; j += blockDim.x) {
+      int32_t u = in.q[i0 + j];
+      S.base[j] = in.qoff[i0 + j];
+      S.u[j] = u;
+      S.adj[j] = __ldg(g.off + u);
+    }
+    if (threadIdx.x == 0) S.base[nv] = (i1 + 1 < in.cnt) ? in.qoff[i1 + 1] : in.D;
+    __syncthreads();
+    const uint32_t nwin = (e_hi - e_lo + 31) >> 5;
+    const uint32_t K = (nwin + nw - 1) / nw;
+    const uint32_t w_lo = e_lo + (uint32_t)warp * K * 32;
+    const uint32_t w_hi = min(w_lo + K * 32, e_hi);
+    if (w_lo < w_hi) {
+      uint32_t j = smem_upper(S.base, nv, w_lo);
+      for (uint32_t b = w_lo; b < w_hi; b += 32) {
+        uint32_t k = j + 1 + lane, bpos = 0;
+        if (k <= nv) {
+          uint32_t bb = S.base[k];
+          if (bb < b + 32) bpos = 1u << (bb - b);
+        }
+        const unsigned mask = __reduce_or_sync(kFull, bpos);
+        const uint32_t jj = min(j + __popc(mask & lanemask_le()), nv - 1);
+        const uint32_t e = b + lane;
+        bool emit = false;
+        int32_t ov = 0;
+        uint32_t od = 0;
+        if (e < w_hi) {
+          const uint32_t idx = S.adj[jj] + (e - S.base[jj]);
+          if (idx < g.m) {
+            const int32_t v = __ldg(g.tgt + idx);
+            fn(S.u[jj], v, idx, emit, ov, od);
+          }
+        }
+        sink.append(S, emit, ov, od);
+        j += __popc(mask);
+        if (j + 1 <= nv && S.base[j + 1] <= b + 32) j++;
+      }
+    }
+    sink.chunk_done(S);
+  }
+}
+
+// Sink that stages into shared memory and flushes into a QueueOut.
+struct StagedSink {
+  QueueOut out;
+  Ctl *ctl;
+  __device__ __forceinline__ void append(PushSmem &S, bool emit, int32_t v, uint32_t d) {
+    stage_append(S, emit, v, d);
+  }
+  __device__ __forceinline__ void chunk_done(PushSmem &S) {
+    __syncthreads();
+    if (S.misc[0] + (S.cap_out >> 1) > S.cap_out) stage_flush(S, out, ctl);
+  }
+  __device__ __forceinline__ void finish(PushSmem &S) { stage_flush(S, out, ctl); }
+};
+
+// Sink that appends directly to a global list with one atomic per warp.
+struct ListSink {
+  int32_t *list;
+  unsigned int *count;
+  uint32_t cap;
+  Ctl *ctl;
+  __device__ __forceinline__ void append(PushSmem &, bool emit, int32_t v, uint32_t) {
+    unsigned bal = __ballot_sync(kFull, emit);
+    if (bal == 0) return;
+    const int lane = threadIdx.x & 31;
+    int leader = __ffs(bal) - 1;
+    uint32_t pos = 0;
+    if (lane == leader) pos = atomicAdd(count, (unsigned)__popc(bal));
+    pos = __shfl_sync(kFull, pos, leader);
+    if (emit) {
+      uint32_t r = pos + __popc(bal & lanemask_lt());
+      if (r < cap) list[r] = v;
+      else raise_error(ctl, GBF_ERR_OVERFLOW, 4);
+    }
+  }
+  __device__ __forceinline__ void chunk_done(PushSmem &) { __syncthreads(); }
+  __device__ __forceinline__ void finish(PushSmem &) {}
+};
+
+// Chunk exponent s (chunk = 256 << s edges) for a frontier of D edges:
+// about four chunks per CTA, capped by the shared-memory capacity Bmax.
+__device__ __forceinline__ int chunk_shift(uint32_t D, int log2Bmax_over_fine) {
+  uint32_t per = D / (4u * gridDim.x);
+  int s = 0;
+  while (s < log2Bmax_over_fine && (kFine << s) < per) s++;
+  return s;
+}
+
+}  // namespace dev
+}  // namespace gbf

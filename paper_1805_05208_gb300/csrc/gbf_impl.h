@@ -1,0 +1,133 @@
+// Internal host-side definitions shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+#include <string>
+
+#include "../../include/gbf.h"
+
+namespace gbf {
+
+// ------------------------------------------------------------ error reporting
+void set_error(const std::string &msg);
+gbf_status cuda_fail(cudaError_t e, const char *what);
+
+#define GBF_CUDA(call)                                   \
+  do {                                                   \
+    cudaError_t _e = (call);                             \
+    if (_e != cudaSuccess) return ::gbf::cuda_fail(_e, #call); \
+  } while (0)
+
+// ------------------------------------------------------------- device structs
+// Control block of one persistent launch.  Zeroed by the host before every
+// launch; every field is touched by the device only through atomics or
+// volatile accesses.
+struct Ctl {
+  unsigned int bar;            // monotone grid-barrier arrival counter
+  int err;                     // gbf_status raised on the device (0 = ok)
+  int err_where;               // where it was raised (debug)
+  int stop;                    // fault injection flag nobody sets
+  unsigned long long fr[3];    // frontier counters (count << 32 | degree sum), by round % 3
+  unsigned long long conv;     // conversion cursor (same packing)
+  // wBFS
+  unsigned int mcnt[2];        // moved-list counts, by round parity
+  int gmin[2];                 // min distance lowered in the round, by parity
+  unsigned int ovf_cnt[2];     // overflow bucket counts
+  int ovf_min[2];              // overflow bucket minimum value
+  // statistics
+  unsigned long long edges_scanned;
+  unsigned long long expanded;
+  unsigned long long reached;
+  unsigned long long relax;
+  unsigned long long inserts;
+  int rounds, push_rounds, pull_rounds, refills;
+};
+
+struct DevGraph {
+  int32_t n;
+  uint32_t m;
+  const uint32_t *off;
+  const int32_t *tgt;
+  const uint32_t *w;
+};
+
+// Device-resident scratch for one query at a time.
+struct Workspace {
+  int32_t n = 0;
+  uint32_t m = 0;
+  size_t bytes = 0;
+  uint32_t *visited = nullptr;   // ceil(n/32) words
+  uint32_t *fbm[2] = {nullptr, nullptr};
+  int32_t *q[2] = {nullptr, nullptr};
+  uint32_t *qoff[2] = {nullptr, nullptr};
+  uint32_t *cs[2] = {nullptr, nullptr};  // chunk starts, one per 256 frontier edges
+  Ctl *ctl = nullptr;
+  int32_t *dist_tmp = nullptr;     // used for host-memory outputs
+  int32_t *parent_tmp = nullptr;
+  // wBFS (lazy)
+  int32_t *stamp = nullptr;
+  int32_t *moved[2] = {nullptr, nullptr};
+  int32_t *slots = nullptr;        // nB * n
+  uint32_t *slot_cnt = nullptr;    // nB
+  int32_t nB = 0;
+  int2 *ovf[2] = {nullptr, nullptr};
+  uint64_t ovf_cap = 0;
+  // MS-BFS (lazy)
+  unsigned long long *ms_seen = nullptr, *ms_visit = nullptr, *ms_next = nullptr;
+  int32_t *ms_dist_tmp = nullptr;   // 64*n for host outputs
+  int32_t *ms_srcs = nullptr;       // 64 device
+  int32_t *ms_srcs_host = nullptr;  // pinned 64
+  cudaGraphExec_t ms_exec = nullptr;
+  const void *ms_exec_key[4] = {nullptr, nullptr, nullptr, nullptr};
+  // pinned host copy of the control block
+  Ctl *ctl_host = nullptr;
+  int last_kind = 0;   // 1 bfs, 2 wbfs, 3 msbfs
+  int last_grid = 0, last_block = 0;
+};
+
+struct Graph {
+  int32_t n = 0;
+  uint32_t m = 0;
+  uint32_t w_max = 0;
+  uint64_t fingerprint = 0;
+  int device = 0;
+  int num_sms = 0;
+  uint32_t *off = nullptr;
+  int32_t *tgt = nullptr;
+  uint32_t *w = nullptr;
+  size_t bytes = 0;
+  Workspace ws;
+  std::mutex mu;   // serialises host calls on the default workspace
+  DevGraph dev() const { return DevGraph{n, m, off, tgt, w}; }
+};
+
+// Resolved options (defaults filled, clamped).
+struct Opts {
+  int block, pull_divisor, heavy_cutoff, bucket_window, dense_wbfs, ctas, pull_serial, inject_wait;
+  long long spin_cap_ns;
+};
+Opts resolve(const gbf_options *o, const Graph &g);
+
+// Workspace management (graph.cu)
+gbf_status ws_ensure_base(Graph &g, Workspace &ws);
+gbf_status ws_ensure_wbfs(Graph &g, Workspace &ws, int nB);
+gbf_status ws_ensure_msbfs(Graph &g, Workspace &ws, bool host_out);
+void ws_free(Workspace &ws);
+gbf_status ws_collect(Workspace &ws, cudaStream_t st, gbf_stats *stats);
+
+// Launchers (bfs.cu / wbfs.cu / msbfs.cu); outputs are device pointers.
+gbf_status launch_bfs(Graph &g, Workspace &ws, int32_t src, int32_t *dist, int32_t *parent,
+                      const Opts &o, cudaStream_t st);
+gbf_status launch_wbfs(Graph &g, Workspace &ws, int32_t src, int32_t *dist, const Opts &o,
+                       cudaStream_t st);
+gbf_status launch_msbfs(Graph &g, Workspace &ws, const int32_t *srcs_host, int32_t k,
+                        int32_t *dist, const Opts &o, cudaStream_t st);
+
+}  // namespace gbf
+
+struct gbf_graph {
+  gbf::Graph g;
+};
