@@ -39,6 +39,10 @@ INF = 2**31 - 1
 WORKLOADS = {
     "wbfs-rmat22": dict(kind="wbfs", graph="rmat", scale=22, ef=16, w=(1, 22), nsrc=8,
                         desc="wBFS, RMAT scale 22 ef16, w in [1,22), 8 seeded sources one at a time"),
+    "wbfs-rmat20": dict(kind="wbfs", graph="rmat", scale=20, ef=16, w=(1, 22), nsrc=8,
+                        desc="wBFS, RMAT scale 20 ef16, w in [1,22), 8 seeded sources (profiling size)"),
+    "bfs-rmat20": dict(kind="bfs", graph="rmat", scale=20, ef=16, w=None, nsrc=8,
+                       desc="BFS (dist+parent), RMAT scale 20 ef16, 8 seeded sources (profiling size)"),
     "bfs-rmat22": dict(kind="bfs", graph="rmat", scale=22, ef=16, w=None, nsrc=8,
                        desc="BFS (dist+parent), RMAT scale 22 ef16, 8 seeded sources"),
     "bfs-rmat26": dict(kind="bfs", graph="rmat", scale=26, ef=16, w=None, nsrc=4,
