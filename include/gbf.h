@@ -184,6 +184,34 @@ gbf_status gbf_wbfs(gbf_graph *g, int32_t src, int32_t *dist, int mem, const gbf
  */
 gbf_status gbf_wait(gbf_graph *g, void *cuda_stream, gbf_stats *stats);
 
+/*
+ * gbf_bfs_noalloc — the same BFS as gbf_bfs for callers that cannot allocate
+ * device memory: for example a process whose device memory is already owned
+ * by another allocator (a framework's caching allocator, a fixed-budget
+ * deployment), or a latency-critical loop where cudaMalloc / cudaFree, which
+ * may synchronise the whole device, are not acceptable.  The paper has no
+ * counterpart; it is a packaging of the BFS of Alg. 1.
+ *   n, m      vertices (1 <= n <= 1,048,576) and arcs (m <= 33,554,432)
+ *   off, tgt  the symmetric CSR graph in DEVICE memory (uint32[n+1], int32[m])
+ *   src       source vertex
+ *   dist      int32[n] in device memory (GBF_INF if unreachable)
+ *   parent    int32[n] in device memory, or NULL
+ *   opt       NULL for defaults
+ *   cuda_stream  stream to run on; the call blocks until the search is done
+ *             and returns the device-side status
+ * The call allocates nothing: its scratch (~18.2 MB) is one fixed array in
+ * the library's device module, held on every GPU that loads the library
+ * until the process exits.  The first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress) with the device current; make that
+ * first call before any stream capture.  All calls share the one array, so
+ * calls that overlap on the GPU (different streams, threads or processes
+ * sharing a context) race and must be serialised by the caller.  Sizes above
+ * the limits return GBF_ERR_INVALID without touching the GPU.
+ */
+gbf_status gbf_bfs_noalloc(int32_t n, uint32_t m, const uint32_t *off, const int32_t *tgt,
+                           int32_t src, int32_t *dist, int32_t *parent, const gbf_options *opt,
+                           void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

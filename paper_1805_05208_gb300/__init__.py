@@ -77,6 +77,7 @@ def _load() -> ctypes.CDLL:
         "gbf_bfs": (S, [P, I32, P, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
         "gbf_wbfs": (S, [P, I32, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
         "gbf_wait": (S, [P, P, ctypes.POINTER(gbf_stats)]),
+        "gbf_bfs_noalloc": (S, [I32, U32, P, P, I32, P, P, ctypes.POINTER(gbf_options), P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -192,6 +193,20 @@ def gbf_wait(h: int, stream=None) -> dict:
     s = gbf_stats()
     _check(_lib.gbf_wait(h, _stream(stream), ctypes.byref(s)), "gbf_wait")
     return s.as_dict()
+
+
+def gbf_bfs_noalloc(n: int, m: int, off, tgt, src: int, dist, parent=None,
+                    opt: Optional[gbf_options] = None, stream=None) -> None:
+    """BFS on a caller-held device CSR with no device allocation (blocks)."""
+    po, mo = _ptr(off)
+    pt, mt = _ptr(tgt)
+    pd, md = _ptr(dist)
+    pp, mp = _ptr(parent)
+    for mm in (mo, mt, md, mp):
+        if mm is not None and mm != DEVICE:
+            raise ValueError("gbf_bfs_noalloc takes device buffers only")
+    _check(_lib.gbf_bfs_noalloc(int(n), int(m), po, pt, int(src), pd, pp, _opt(opt),
+                                _stream(stream)), "gbf_bfs_noalloc")
 
 
 class Graph:
