@@ -150,17 +150,34 @@ def bytes_model(kind, n, st):
     word, random or not), from the device statistics of the query."""
     E, V, R, I = st["edges_scanned"], st["vertices_expanded"], st["relaxations"], st["bucket_inserts"]
     if kind == "wbfs":
-        # init D + stamp (8n); per frontier vertex q,qoff,off[u] + queue write (20);
-        # per arc tgt,w,D[v] (12); per successful writeMin: atomicMin, stamp,
-        # moved append, then filing: moved read, D, offsets, slot write (32);
-        # per bucket entry extracted: slot, D, offsets (16)
-        return 8 * n + 20 * V + 12 * E + 32 * R + 16 * I
+        # init D (4n); per bucket entry read at extraction: ring slot, D[v],
+        # offsets pair (16; entries = filings I, stale ones included); per
+        # scanned arc: tgt, w, D[v] (12); per successful writeMin: atomicMin
+        # and the bucket write (8); per heavy vertex: queue + degree prefix
+        # written and read (16)
+        return 4 * n + 16 * I + 12 * E + 8 * R + 16 * st["heavy_vertices"]
     # BFS: init D, parent (8n) + visited bitmap (n/8); per frontier vertex or
     # pull candidate: queue/offset reads (12); per arc: target + bitmap word (8);
     # per reached vertex: D, parent, offsets, queue+qoff write (24); bitmaps per
     # dense round (3 passes of n/8)
     return 8 * n + n // 8 + 12 * V + 8 * E + 24 * st["vertices_reached"] + \
         3 * (n // 8) * st["pull_rounds"]
+
+
+def trace_summary(tr):
+    """Per-kind round counts and device time of one query's round trace."""
+    out, prev = {}, 0
+    names = {1: "sparse", 2: "dense", 3: "sparse+heavy", 4: "conversion"}
+    for (_, kind, fr, fe, t, _tm) in tr:
+        k = names.get(kind, str(kind))
+        d = out.setdefault(k, {"rounds": 0, "us": 0.0, "frontier": 0})
+        d["rounds"] += 1
+        d["us"] += (t - prev) / 1e3
+        d["frontier"] += fr
+        prev = t
+    for d in out.values():
+        d["us"] = round(d["us"], 1)
+    return {"rounds": len(tr), "end_us": round(prev / 1e3, 1), "by_kind": out}
 
 
 def cpu_reference_sample(g, wl, srcs, budget_s=15.0, max_queries=None):
@@ -272,6 +289,8 @@ def main():
             if w == 0:
                 stats.append(gb.gbf_wait(graph.h, stream))
                 te.append(traversed_edges(g, outs[i].cpu().numpy()))
+                if i == 0:
+                    trace0 = gb.gbf_trace(graph.h)
     gb.gbf_wait(graph.h, stream)
     te_step = sum(te)
 
@@ -371,7 +390,8 @@ def main():
                       "pull_rounds": [s["pull_rounds"] for s in stats],
                       "edges_scanned": sum(s["edges_scanned"] for s in stats),
                       "traversed_edges_per_step": te_step,
-                      "grid_ctas": stats[0]["grid_ctas"], "block": stats[0]["block"]},
+                      "grid_ctas": stats[0]["grid_ctas"], "block": stats[0]["block"],
+                      "query0_trace": trace_summary(trace0)},
         }
         print(json.dumps(line))
     graph.close()

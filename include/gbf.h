@@ -72,9 +72,9 @@ typedef struct gbf_graph gbf_graph;
  *                 out-degree sum exceeds m / pull_divisor (default 20; -1 = push only)
  *   heavy_cutoff  largest number of frontier edges one CTA processes as one
  *                 block of the blocked sparse edgeMap; a vertex with more
- *                 edges is split over several CTAs (power of two, 256..4096, default 1024)
+ *                 edges is split over several CTAs (power of two, 256..4096, default 512)
  *   bucket_window number of open buckets nB of the wBFS bucket structure
- *                 (default max weight + 1; smaller values exercise the overflow bucket)
+ *                 (1..256, default min(max weight + 1, 256); values <= max weight use the overflow bucket)
  *   dense_wbfs    1 = let wBFS switch to a dense edgeMap for dense buckets (default 0)
  *   spin_cap_us   time limit of every bounded device wait, microseconds (default 5,000,000)
  *   counters      reserved (statistics are always collected)
@@ -108,6 +108,7 @@ typedef struct {
   int64_t relaxations;       /* wBFS: successful writeMin calls */
   int64_t bucket_inserts;    /* wBFS: entries appended to buckets (incl. overflow) */
   int64_t refills;           /* wBFS: overflow-bucket refills */
+  int64_t heavy_vertices;    /* frontier vertices expanded by the blocked edgeMap pass */
   int32_t grid_ctas;         /* CTAs of the persistent launch */
   int32_t block;             /* threads per CTA */
   int32_t device_error;      /* gbf_status reported by the device */
@@ -183,6 +184,25 @@ gbf_status gbf_wbfs(gbf_graph *g, int32_t src, int32_t *dist, int mem, const gbf
  * buffers; fills *stats if non-NULL.
  */
 gbf_status gbf_wait(gbf_graph *g, void *cuda_stream, gbf_stats *stats);
+
+/* One record per round of the last query (see gbf_trace). */
+typedef struct {
+  int32_t round;          /* 1-based round (BFS level or wBFS bucket round) */
+  int32_t kind;           /* 1 sparse, 2 dense, 3 sparse + heavy pass, 4 conversion */
+  uint32_t frontier;      /* frontier vertices (wBFS: bucket entries, stale ones included) */
+  uint32_t frontier_edges;/* out-degree sum of the frontier when known (0 otherwise) */
+  int64_t t_ns;           /* device time at the end of the round, since the kernel started */
+  int64_t t_mid_ns;       /* end of the round's first phase when it has two (0 otherwise) */
+} gbf_round_trace;
+
+/*
+ * gbf_trace — per-round device timeline of the last gbf_bfs / gbf_wbfs on g
+ * (the round structure of Alg. 1 / Alg. 3 as it ran: direction chosen,
+ * frontier size, time).  Call after the query completed (host buffers, or
+ * after gbf_wait).  Copies min(rounds, cap) records to out and their number
+ * to *count.
+ */
+gbf_status gbf_trace(gbf_graph *g, gbf_round_trace *out, int32_t cap, int32_t *count);
 
 /*
  * gbf_bfs_noalloc — the same BFS as gbf_bfs for callers that cannot allocate

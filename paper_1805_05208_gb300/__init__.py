@@ -50,12 +50,19 @@ class gbf_stats(ctypes.Structure):
                 ("pull_rounds", ctypes.c_int64), ("edges_scanned", ctypes.c_int64),
                 ("vertices_expanded", ctypes.c_int64), ("vertices_reached", ctypes.c_int64),
                 ("relaxations", ctypes.c_int64), ("bucket_inserts", ctypes.c_int64),
-                ("refills", ctypes.c_int64), ("grid_ctas", ctypes.c_int32),
+                ("refills", ctypes.c_int64), ("heavy_vertices", ctypes.c_int64),
+                ("grid_ctas", ctypes.c_int32),
                 ("block", ctypes.c_int32), ("device_error", ctypes.c_int32),
                 ("reserved", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class gbf_round_trace(ctypes.Structure):
+    _fields_ = [("round", ctypes.c_int32), ("kind", ctypes.c_int32), ("frontier", ctypes.c_uint32),
+                ("frontier_edges", ctypes.c_uint32), ("t_ns", ctypes.c_int64),
+                ("t_mid_ns", ctypes.c_int64)]
 
 
 def _load() -> ctypes.CDLL:
@@ -77,6 +84,7 @@ def _load() -> ctypes.CDLL:
         "gbf_bfs": (S, [P, I32, P, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
         "gbf_wbfs": (S, [P, I32, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
         "gbf_wait": (S, [P, P, ctypes.POINTER(gbf_stats)]),
+        "gbf_trace": (S, [P, ctypes.POINTER(gbf_round_trace), I32, ctypes.POINTER(I32)]),
         "gbf_bfs_noalloc": (S, [I32, U32, P, P, I32, P, P, ctypes.POINTER(gbf_options), P]),
     }
     for name, (res, args) in sig.items():
@@ -193,6 +201,15 @@ def gbf_wait(h: int, stream=None) -> dict:
     s = gbf_stats()
     _check(_lib.gbf_wait(h, _stream(stream), ctypes.byref(s)), "gbf_wait")
     return s.as_dict()
+
+
+def gbf_trace(h: int, cap: int = 1 << 16) -> list:
+    """Per-round records (round, kind, frontier, frontier_edges, t_ns, t_mid_ns) of the last query."""
+    buf = (gbf_round_trace * cap)()
+    cnt = ctypes.c_int32()
+    _check(_lib.gbf_trace(h, buf, cap, ctypes.byref(cnt)), "gbf_trace")
+    return [(r.round, r.kind, r.frontier, r.frontier_edges, r.t_ns, r.t_mid_ns)
+            for r in buf[:cnt.value]]
 
 
 def gbf_bfs_noalloc(n: int, m: int, off, tgt, src: int, dist, parent=None,

@@ -35,9 +35,12 @@ struct BfsParams {
   uint32_t *cs[2];
   uint32_t cs_cap;
   Ctl *ctl;
+  TraceRec *trace;
+  int trace_cap;
   int pull_divisor;
   int log2_bmax_fine;  // log2(Bmax / 256)
   int bmax;
+  int cap;             // staging capacity
   int pull_serial;
   int inject_wait;
   long long cap_ns;
@@ -45,26 +48,49 @@ struct BfsParams {
 
 namespace {
 
-// Sparse-direction Update of Alg. 1: test-and-set on the visited bit.
+// Sparse-direction Update of Alg. 1: test-and-set on the visited bit; the
+// winner writes D and the parent.  kU windows at a time: all target loads,
+// then all bitmap loads, then the test-and-sets, then the winners' degrees.
 struct BfsPushFn {
   const uint32_t *off;
+  const int32_t *tgt;
   uint32_t *visited;
   int32_t *dist, *parent;
   int32_t level;
   unsigned long long reached;
-  __device__ __forceinline__ void operator()(int32_t u, int32_t v, uint32_t, bool &emit,
-                                             int32_t &ov, uint32_t &od) {
-    const uint32_t bit = 1u << (v & 31);
-    uint32_t *wp = visited + (v >> 5);
-    if (*wp & bit) return;
-    if (atomicOr(wp, bit) & bit) return;
-    dist[v] = level;
-    if (parent) parent[v] = u;
-    reached++;
-    const uint32_t d = __ldg(off + v + 1) - __ldg(off + v);
-    emit = d >= 2;
-    ov = v;
-    od = d;
+  template <class Sink>
+  __device__ __forceinline__ void batch(const bool *val, const int32_t *u, const uint32_t *idx,
+                                        Sink &sink, PushSmem &S) {
+    int32_t v[kU];
+    uint32_t wd[kU];
+#pragma unroll
+    for (int r = 0; r < kU; r++) v[r] = val[r] ? __ldg(tgt + idx[r]) : 0;
+#pragma unroll
+    for (int r = 0; r < kU; r++) wd[r] = val[r] ? visited[v[r] >> 5] : ~0u;
+    bool win[kU];
+#pragma unroll
+    for (int r = 0; r < kU; r++) {
+      const uint32_t bit = 1u << (v[r] & 31);
+      win[r] = false;
+      if (!(wd[r] & bit)) win[r] = !(atomicOr(visited + (v[r] >> 5), bit) & bit);
+    }
+    uint32_t a[kU], z[kU];
+#pragma unroll
+    for (int r = 0; r < kU; r++) {
+      a[r] = z[r] = 0;
+      if (win[r]) {
+        dist[v[r]] = level;
+        if (parent) parent[v[r]] = u[r];
+        a[r] = __ldg(off + v[r]);
+        z[r] = __ldg(off + v[r] + 1);
+        reached++;
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < kU; r++) {
+      const uint32_t d = z[r] - a[r];
+      sink.append(S, win[r] && d >= 2, v[r], d);
+    }
   }
 };
 
@@ -198,7 +224,7 @@ __device__ void bitmap_to_queue(const BfsParams &P, const uint32_t *fb, PushSmem
 __global__ void __launch_bounds__(1024) bfs_kernel(BfsParams P) {
   extern __shared__ unsigned long long smem_raw[];
   __shared__ int s_flag;
-  PushSmem S = carve_push_smem(smem_raw, P.bmax);
+  PushSmem S = carve_push_smem(smem_raw, SmemShape{P.bmax, P.cap, 0, 0});
   if (threadIdx.x == 0) S.misc[0] = 0;
   Ctl *ctl = P.ctl;
   Barrier bar{0u, P.cap_ns};
@@ -207,6 +233,7 @@ __global__ void __launch_bounds__(1024) bfs_kernel(BfsParams P) {
   const uint32_t nwords = ((uint32_t)g.n + 31) >> 5;
   const int32_t src = P.src;
   unsigned long long scanned = 0, reached = 0, expanded = 0;
+  const unsigned long long t_start = globaltimer();
 
   // Initialisation (Alg. 1 line 1 and BFS line 1): D = inf, Fl = 0, then the source.
   for (uint32_t i = gt; i < (uint32_t)g.n; i += gs) {
@@ -263,12 +290,13 @@ __global__ void __launch_bounds__(1024) bfs_kernel(BfsParams P) {
     }
     if (!fmt_bitmap) {
       QueueIn in{P.q[qb], P.qoff[qb], P.cs[qb], cnt, D};
-      BfsPushFn fn{g.off, P.visited, P.dist, P.parent, level, 0};
+      BfsPushFn fn{g.off, g.tgt, P.visited, P.dist, P.parent, level, 0};
       StagedSink sink{QueueOut{P.q[qb ^ 1], P.qoff[qb ^ 1], P.cs[qb ^ 1], outc, (uint32_t)g.n,
                                P.cs_cap},
                       ctl};
-      const int s = chunk_shift(D, P.log2_bmax_fine);
-      blocked_edge_map(g, in, s, S, fn, sink, ctl);
+      // every queued vertex has degree >= 2
+      const int s = chunk_shift(D, (uint32_t)P.bmax, 2u);
+      blocked_edge_map(g, in, s, (uint32_t)P.bmax, S, fn, sink, ctl);
       sink.finish(S);
       reached += fn.reached;
       qb ^= 1;
@@ -279,6 +307,9 @@ __global__ void __launch_bounds__(1024) bfs_kernel(BfsParams P) {
     }
     if (!grid_sync(ctl, bar, &s_flag)) break;
     fr = ld_vol(*outc);
+    if (P.trace && blockIdx.x == 0 && threadIdx.x == 0 && level <= P.trace_cap)
+      P.trace[level - 1] = TraceRec{level, fmt_bitmap ? 2 : 1, cnt, D,
+                                    (long long)(globaltimer() - t_start), 0};
     level++;
   }
   // statistics
@@ -307,15 +338,18 @@ gbf_status launch_bfs(Graph &g, Workspace &ws, int32_t src, int32_t *dist, int32
   }
   P.cs_cap = (uint32_t)(((uint64_t)g.m + kFine - 1) / kFine + 2);
   P.ctl = ws.ctl;
+  P.trace = ws.trace;
+  P.trace_cap = ws.trace_cap;
   P.pull_divisor = o.pull_divisor;
   P.bmax = o.heavy_cutoff;
+  P.cap = 2 * kU * o.block;
   int l = 0;
   while ((kFine << l) < (uint32_t)o.heavy_cutoff) l++;
   P.log2_bmax_fine = l;
   P.pull_serial = o.pull_serial;
   P.inject_wait = o.inject_wait;
   P.cap_ns = o.spin_cap_ns;
-  const size_t smem = push_smem_bytes(o.heavy_cutoff);
+  const size_t smem = push_smem_bytes(SmemShape{P.bmax, P.cap, 0, 0});
   GBF_CUDA(cudaFuncSetAttribute(bfs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem));
   int per_sm = 0;
@@ -327,6 +361,7 @@ gbf_status launch_bfs(Graph &g, Workspace &ws, int32_t src, int32_t *dist, int32
   int grid = per_sm * g.num_sms;
   if (o.ctas > 0 && o.ctas < grid) grid = o.ctas;
   GBF_CUDA(cudaMemsetAsync(ws.ctl, 0, sizeof(Ctl), st));
+  if (ws.trace) GBF_CUDA(cudaMemsetAsync(ws.trace, 0, sizeof(TraceRec) * (size_t)ws.trace_cap, st));
   void *args[] = {&P};
   GBF_CUDA(cudaLaunchCooperativeKernel((const void *)bfs_kernel, dim3(grid), dim3(o.block), args,
                                        smem, st));

@@ -170,12 +170,16 @@ __device__ __forceinline__ int block_min_i32(int x, int *s_tmp) {
 }
 
 // ---------------------------------------------------- shared-memory layout
-// Dynamic shared memory of the frontier kernels, for chunks of up to Bmax
-// frontier edges:
-//   base/u/adj  [Bmax+2]   per frontier vertex of the chunk: edge-space start,
-//                          vertex id, CSR offset of its first arc
-//   out_v/out_d [2*Bmax]   staged live neighbours and their degrees
-//   pref        [2*Bmax]   exclusive prefix of out_d during a flush
+constexpr int kU = 4;  // 32-edge windows a warp keeps in flight per step
+
+// Dynamic shared memory of the frontier kernels:
+//   base/u/adj  [Bmax+2]   per frontier vertex of the current chunk: start in
+//                          the chunk's edge space, vertex id, CSR offset of
+//                          its first arc
+//   out_v/out_d [cap]      staged next-frontier vertices and their degrees
+//   pref        [cap]      exclusive prefix of out_d (or ranks) during a flush
+//   fv/fs       [cap]      staged bucket filings: vertex, slot (<0: overflow)
+//   hist/gbase  [nB]       per-slot counts and reserved positions of a flush
 struct PushSmem {
   uint32_t *base;
   int32_t *u;
@@ -183,16 +187,29 @@ struct PushSmem {
   int32_t *out_v;
   uint32_t *out_d;
   uint32_t *pref;
-  uint32_t *misc;  // [0] n_out, [1] pos, [2] dpos, [3] flag, [8..41] scan tmp
+  int32_t *fv;
+  int32_t *fs;
+  uint32_t *hist;
+  uint32_t *gbase;
+  uint32_t *misc;  // [0] n_out [1] pos [2] dpos [3] flag [4] n_filed [5] n_ovf [6] ovf pos [7] ovf min, [8..41] scan tmp
   unsigned long long *misc64;  // 32 entries
-  uint32_t cap_out;            // 2*Bmax
+  uint32_t cap_out;
 };
 
-__host__ __device__ inline size_t push_smem_bytes(int Bmax) {
-  return sizeof(uint32_t) * (size_t)(3 * (Bmax + 2) + 3 * 2 * Bmax + 64) + 8 * 32 + 16;
+struct SmemShape {
+  int bmax;   // largest chunk of the blocked edgeMap
+  int cap;    // staging capacity (>= 2 * kU * blockDim)
+  int filed;  // 1: reserve the bucket-filing stage
+  int nB;     // bucket slots (histogram size)
+};
+
+__host__ __device__ inline size_t push_smem_bytes(const SmemShape &sh) {
+  size_t w = 64 + 3 * (size_t)(sh.bmax + 2) + 3 * (size_t)sh.cap;
+  if (sh.filed) w += 2 * (size_t)sh.cap + 2 * (size_t)sh.nB;
+  return 8 * 32 + 4 * w + 16;
 }
 
-__device__ __forceinline__ PushSmem carve_push_smem(void *raw, int Bmax) {
+__device__ __forceinline__ PushSmem carve_push_smem(void *raw, const SmemShape &sh) {
   PushSmem S;
   unsigned long long *p64 = (unsigned long long *)raw;
   S.misc64 = p64;
@@ -200,17 +217,29 @@ __device__ __forceinline__ PushSmem carve_push_smem(void *raw, int Bmax) {
   S.misc = p;
   p += 64;
   S.base = p;
-  p += Bmax + 2;
+  p += sh.bmax + 2;
   S.u = (int32_t *)p;
-  p += Bmax + 2;
+  p += sh.bmax + 2;
   S.adj = p;
-  p += Bmax + 2;
+  p += sh.bmax + 2;
   S.out_v = (int32_t *)p;
-  p += 2 * Bmax;
+  p += sh.cap;
   S.out_d = p;
-  p += 2 * Bmax;
+  p += sh.cap;
   S.pref = p;
-  S.cap_out = 2u * (uint32_t)Bmax;
+  p += sh.cap;
+  S.fv = S.fs = nullptr;
+  S.hist = S.gbase = nullptr;
+  if (sh.filed) {
+    S.fv = (int32_t *)p;
+    p += sh.cap;
+    S.fs = (int32_t *)p;
+    p += sh.cap;
+    S.hist = p;
+    p += sh.nB;
+    S.gbase = p;
+  }
+  S.cap_out = (uint32_t)sh.cap;
   return S;
 }
 
@@ -308,23 +337,78 @@ __device__ __forceinline__ uint32_t smem_upper(const uint32_t *base, uint32_t nv
   return lo;
 }
 
+// CTA-collective walk over the edges [e_lo, e_hi) of a chunk whose nv
+// frontier vertices (each with at least one edge) are described by
+// S.base/u/adj, base[nv] being the end of the last one.  Each warp takes a
+// contiguous run of K windows of 32 consecutive edges (coalesced target
+// loads); it locates the vertex of each lane from the boundaries falling in
+// the window (one shared load per lane and a warp OR).  Every step hands kU
+// windows to fn.batch (which issues all their loads before using them) and
+// then runs sink.step_done, where the CTA may flush its staging buffers.
+template <class Fn, class Sink>
+__device__ __forceinline__ void walk_chunk(PushSmem &S, uint32_t m, uint32_t nv, uint32_t e_lo,
+                                           uint32_t e_hi, Fn &fn, Sink &sink) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const uint32_t nwin = (e_hi - e_lo + 31) >> 5;
+  uint32_t K = (nwin + nw - 1) / nw;
+  K = (K + kU - 1) / kU * kU;
+  const uint32_t w_lo = e_lo + (uint32_t)warp * K * 32;
+  const uint32_t w_hi = min(w_lo + K * 32, e_hi);
+  uint32_t j = (w_lo < w_hi) ? smem_upper(S.base, nv, w_lo) : 0u;
+  for (uint32_t st = 0; st < K; st += kU) {
+    bool val[kU];
+    int32_t uu[kU];
+    uint32_t idx[kU];
+#pragma unroll
+    for (int r = 0; r < kU; r++) {
+      const uint32_t b = w_lo + (st + r) * 32;
+      const bool live = b < w_hi;  // warp-uniform
+      unsigned bpos = 0;
+      if (live) {
+        const uint32_t k = j + 1 + lane;
+        if (k <= nv) {
+          const uint32_t bb = S.base[k];
+          if (bb < b + 32) bpos = 1u << (bb - b);
+        }
+      }
+      const unsigned mask = __reduce_or_sync(kFull, bpos);
+      const uint32_t e = b + lane;
+      val[r] = live && e < w_hi;
+      idx[r] = 0u;
+      uu[r] = 0;
+      if (val[r]) {
+        const uint32_t jj = min(j + __popc(mask & lanemask_le()), nv - 1);
+        idx[r] = S.adj[jj] + (e - S.base[jj]);
+        uu[r] = S.u[jj];
+        val[r] = idx[r] < m;
+      }
+      if (live) {
+        j += __popc(mask);
+        if (j + 1 <= nv && S.base[j + 1] <= b + 32) j++;
+      }
+    }
+    fn.batch(val, uu, idx, sink, S);
+    sink.step_done(S);
+  }
+}
+
 // Blocked sparse edgeMap over the frontier `in` with chunks of B = 256 << s
-// edges.  For every frontier arc (u, v) at CSR index idx, fn(u, v, idx, emit,
-// out_v, out_d) is called by one lane (valid lanes only) and may request an
-// append; Sink::append is warp-collective, Sink::chunk_done CTA-collective.
-template <class EdgeFn, class Sink>
+// edges located through the chunk-start table (edgeMapBlocked, Alg. 2).  A
+// chunk may span at most bmax + 1 frontier vertices (the shared arrays);
+// callers bound s by the smallest degree in the queue.
+template <class Fn, class Sink>
 __device__ __forceinline__ void blocked_edge_map(const DevGraph &g, const QueueIn &in, int s,
-                                                 PushSmem &S, EdgeFn &fn, Sink &sink, Ctl *ctl) {
+                                                 uint32_t bmax, PushSmem &S, Fn &fn, Sink &sink,
+                                                 Ctl *ctl) {
   const uint32_t B = kFine << s;
   const uint32_t nfine = (in.D + kFine - 1) >> kFineLog;
   const uint32_t nch = (in.D + B - 1) / B;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (uint32_t c = blockIdx.x; c < nch; c += gridDim.x) {
     const uint32_t e_lo = c * B, e_hi = min(e_lo + B, in.D);
     const uint32_t f1 = (c + 1) << s;
     const uint32_t i0 = in.cs[c << s];
     const uint32_t i1 = (f1 < nfine) ? in.cs[f1] : in.cnt - 1;
-    if (i1 < i0 || i1 >= in.cnt || i1 - i0 > B) {  // inconsistent table: never expected
+    if (i1 < i0 || i1 >= in.cnt || i1 - i0 > bmax) {  // inconsistent table: never expected
       if (threadIdx.x == 0) raise_error(ctl, GBF_ERR_OVERFLOW, 3);
       continue;
     }
@@ -337,37 +421,7 @@ __device__ __forceinline__ void blocked_edge_map(const DevGraph &g, const QueueI
     }
     if (threadIdx.x == 0) S.base[nv] = (i1 + 1 < in.cnt) ? in.qoff[i1 + 1] : in.D;
     __syncthreads();
-    const uint32_t nwin = (e_hi - e_lo + 31) >> 5;
-    const uint32_t K = (nwin + nw - 1) / nw;
-    const uint32_t w_lo = e_lo + (uint32_t)warp * K * 32;
-    const uint32_t w_hi = min(w_lo + K * 32, e_hi);
-    if (w_lo < w_hi) {
-      uint32_t j = smem_upper(S.base, nv, w_lo);
-      for (uint32_t b = w_lo; b < w_hi; b += 32) {
-        uint32_t k = j + 1 + lane, bpos = 0;
-        if (k <= nv) {
-          uint32_t bb = S.base[k];
-          if (bb < b + 32) bpos = 1u << (bb - b);
-        }
-        const unsigned mask = __reduce_or_sync(kFull, bpos);
-        const uint32_t jj = min(j + __popc(mask & lanemask_le()), nv - 1);
-        const uint32_t e = b + lane;
-        bool emit = false;
-        int32_t ov = 0;
-        uint32_t od = 0;
-        if (e < w_hi) {
-          const uint32_t idx = S.adj[jj] + (e - S.base[jj]);
-          if (idx < g.m) {
-            const int32_t v = __ldg(g.tgt + idx);
-            fn(S.u[jj], v, idx, emit, ov, od);
-          }
-        }
-        sink.append(S, emit, ov, od);
-        j += __popc(mask);
-        if (j + 1 <= nv && S.base[j + 1] <= b + 32) j++;
-      }
-    }
-    sink.chunk_done(S);
+    walk_chunk(S, g.m, nv, e_lo, e_hi, fn, sink);
   }
 }
 
@@ -378,43 +432,22 @@ struct StagedSink {
   __device__ __forceinline__ void append(PushSmem &S, bool emit, int32_t v, uint32_t d) {
     stage_append(S, emit, v, d);
   }
-  __device__ __forceinline__ void chunk_done(PushSmem &S) {
+  __device__ __forceinline__ void step_done(PushSmem &S) {
     __syncthreads();
-    if (S.misc[0] + (S.cap_out >> 1) > S.cap_out) stage_flush(S, out, ctl);
+    if (S.misc[0] + kU * blockDim.x > S.cap_out) stage_flush(S, out, ctl);
   }
   __device__ __forceinline__ void finish(PushSmem &S) { stage_flush(S, out, ctl); }
 };
 
-// Sink that appends directly to a global list with one atomic per warp.
-struct ListSink {
-  int32_t *list;
-  unsigned int *count;
-  uint32_t cap;
-  Ctl *ctl;
-  __device__ __forceinline__ void append(PushSmem &, bool emit, int32_t v, uint32_t) {
-    unsigned bal = __ballot_sync(kFull, emit);
-    if (bal == 0) return;
-    const int lane = threadIdx.x & 31;
-    int leader = __ffs(bal) - 1;
-    uint32_t pos = 0;
-    if (lane == leader) pos = atomicAdd(count, (unsigned)__popc(bal));
-    pos = __shfl_sync(kFull, pos, leader);
-    if (emit) {
-      uint32_t r = pos + __popc(bal & lanemask_lt());
-      if (r < cap) list[r] = v;
-      else raise_error(ctl, GBF_ERR_OVERFLOW, 4);
-    }
-  }
-  __device__ __forceinline__ void chunk_done(PushSmem &) { __syncthreads(); }
-  __device__ __forceinline__ void finish(PushSmem &) {}
-};
-
-// Chunk exponent s (chunk = 256 << s edges) for a frontier of D edges:
-// about four chunks per CTA, capped by the shared-memory capacity Bmax.
-__device__ __forceinline__ int chunk_shift(uint32_t D, int log2Bmax_over_fine) {
-  uint32_t per = D / (4u * gridDim.x);
+// Chunk exponent s (chunk = 256 << s edges) for a frontier of D edges whose
+// vertices all have at least min_deg edges: about four chunks per CTA, and a
+// chunk never spans more than bmax + 1 vertices (B <= bmax * min_deg), nor
+// more than 2^16 edges.
+__device__ __forceinline__ int chunk_shift(uint32_t D, uint32_t bmax, uint32_t min_deg) {
+  const uint32_t per = D / (4u * gridDim.x);
+  const unsigned long long cap = min((unsigned long long)bmax * max(min_deg, 1u), 65536ull);
   int s = 0;
-  while (s < log2Bmax_over_fine && (kFine << s) < per) s++;
+  while ((unsigned long long)(kFine << (s + 1)) <= cap && (kFine << s) < per) s++;
   return s;
 }
 

@@ -37,13 +37,27 @@ struct Ctl {
   int gmin[2];                 // min distance lowered in the round, by parity
   unsigned int ovf_cnt[2];     // overflow bucket counts
   int ovf_min[2];              // overflow bucket minimum value
+  unsigned int imask[3][32];   // buckets filed into during round t, by t % 3 (one bit per slot)
   // statistics
   unsigned long long edges_scanned;
   unsigned long long expanded;
   unsigned long long reached;
   unsigned long long relax;
   unsigned long long inserts;
+  unsigned long long heavy;
   int rounds, push_rounds, pull_rounds, refills;
+};
+
+// One record per round of a persistent launch, written by CTA 0 after the
+// round's last barrier (kind: 1 sparse, 2 dense, 3 sparse + heavy pass,
+// 4 conversion); t_ns is %globaltimer time since the kernel started.
+struct TraceRec {
+  int32_t round;
+  int32_t kind;
+  uint32_t frontier;
+  uint32_t frontier_edges;
+  long long t_ns;
+  long long t_mid_ns;  // end of the round's first phase (0 if single-phase)
 };
 
 struct DevGraph {
@@ -67,10 +81,10 @@ struct Workspace {
   Ctl *ctl = nullptr;
   int32_t *dist_tmp = nullptr;     // used for host-memory outputs
   int32_t *parent_tmp = nullptr;
+  TraceRec *trace = nullptr;
+  int trace_cap = 0;
   // wBFS (lazy)
-  int32_t *stamp = nullptr;
-  int32_t *moved[2] = {nullptr, nullptr};
-  int32_t *slots = nullptr;        // nB * n
+  int32_t *slots = nullptr;        // nB * n (ring buffers)
   uint32_t *slot_cnt = nullptr;    // nB
   int32_t nB = 0;
   int2 *ovf[2] = {nullptr, nullptr};

@@ -179,6 +179,8 @@ gbf_status ws_ensure_base(Graph &g, Workspace &ws) {
   GBF_TRY(dmalloc(&ws.dist_tmp, n, acc));
   GBF_TRY(dmalloc(&ws.parent_tmp, n, acc));
   GBF_TRY(dmalloc(&ws.ctl, 1, acc));
+  ws.trace_cap = 1 << 16;
+  GBF_TRY(dmalloc(&ws.trace, (size_t)ws.trace_cap, acc));
   GBF_CUDA(cudaMallocHost((void **)&ws.ctl_host, sizeof(Ctl)));
   memset(ws.ctl_host, 0, sizeof(Ctl));
   ws.bytes += acc;
@@ -189,11 +191,6 @@ gbf_status ws_ensure_wbfs(Graph &g, Workspace &ws, int nB) {
   GBF_TRY(ws_ensure_base(g, ws));
   const size_t n = (size_t)g.n;
   size_t acc = 0;
-  if (!ws.stamp) {
-    GBF_TRY(dmalloc(&ws.stamp, n, acc));
-    GBF_TRY(dmalloc(&ws.moved[0], n, acc));
-    GBF_TRY(dmalloc(&ws.moved[1], n, acc));
-  }
   if (ws.nB != nB) {
     if (ws.slots) {
       cudaFree(ws.slots);
@@ -228,8 +225,7 @@ gbf_status ws_ensure_wbfs(Graph &g, Workspace &ws, int nB) {
 
 void ws_free(Workspace &ws) {
   void *ptrs[] = {ws.visited, ws.fbm[0], ws.fbm[1], ws.q[0], ws.q[1], ws.qoff[0], ws.qoff[1],
-                  ws.cs[0], ws.cs[1], ws.ctl, ws.dist_tmp, ws.parent_tmp, ws.stamp, ws.moved[0],
-                  ws.moved[1], ws.slots, ws.slot_cnt, ws.ovf[0], ws.ovf[1], ws.ms_seen,
+                  ws.cs[0], ws.cs[1], ws.ctl, ws.dist_tmp, ws.parent_tmp, ws.trace, ws.slots, ws.slot_cnt, ws.ovf[0], ws.ovf[1], ws.ms_seen,
                   ws.ms_visit, ws.ms_next, ws.ms_dist_tmp, ws.ms_srcs};
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -254,6 +250,7 @@ gbf_status ws_collect(Workspace &ws, cudaStream_t st, gbf_stats *stats) {
     stats->relaxations = (int64_t)c.relax;
     stats->bucket_inserts = (int64_t)c.inserts;
     stats->refills = c.refills;
+    stats->heavy_vertices = (int64_t)c.heavy;
     stats->grid_ctas = ws.last_grid;
     stats->block = ws.last_block;
     stats->device_error = c.err;
@@ -279,7 +276,7 @@ gbf_status gbf_options_default(gbf_options *opt) {
   memset(opt, 0, sizeof(*opt));
   opt->block = 256;
   opt->pull_divisor = 20;
-  opt->heavy_cutoff = 1024;
+  opt->heavy_cutoff = 512;
   opt->bucket_window = 0;
   opt->dense_wbfs = 0;
   opt->spin_cap_us = 5000000;
@@ -452,13 +449,28 @@ gbf_status gbf_wbfs(gbf_graph *h, int32_t src, int32_t *dist, int mem, const gbf
   std::lock_guard<std::mutex> lk(g.mu);
   const Opts o = resolve(opt, g);
   int nB = o.bucket_window > 0 ? o.bucket_window : (int)std::max<uint32_t>(g.w_max + 1, 2);
-  nB = std::min(nB, 1 << 16);
+  nB = std::min(nB, 256);
   GBF_TRY(ws_ensure_wbfs(g, g.ws, nB));
   int32_t *dd = mem == GBF_HOST ? g.ws.dist_tmp : dist;
   GBF_TRY(launch_wbfs(g, g.ws, src, dd, o, st));
   if (mem == GBF_DEVICE) return GBF_OK;
   GBF_CUDA(cudaMemcpyAsync(dist, dd, sizeof(int32_t) * (size_t)g.n, cudaMemcpyDeviceToHost, st));
   return ws_collect(g.ws, st, nullptr);
+}
+
+gbf_status gbf_trace(gbf_graph *h, gbf_round_trace *out, int32_t cap, int32_t *count) {
+  if (!h || !count || (cap > 0 && !out)) return set_error("NULL argument"), GBF_ERR_INVALID;
+  Workspace &ws = h->g.ws;
+  *count = 0;
+  if (!ws.trace) return GBF_OK;
+  const int rounds = std::min(ws.ctl_host ? ws.ctl_host->rounds : 0, ws.trace_cap);
+  const int k = std::min(rounds, std::max(cap, 0));
+  if (k > 0) {
+    static_assert(sizeof(TraceRec) == sizeof(gbf_round_trace), "trace record layout");
+    GBF_CUDA(cudaMemcpy(out, ws.trace, sizeof(TraceRec) * (size_t)k, cudaMemcpyDeviceToHost));
+  }
+  *count = k;
+  return GBF_OK;
 }
 
 gbf_status gbf_wait(gbf_graph *h, void *cuda_stream, gbf_stats *stats) {

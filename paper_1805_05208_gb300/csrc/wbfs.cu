@@ -1,28 +1,37 @@
 // Weighted BFS (integral-weight SSSP, §4; Alg. 3) as one persistent
-// cooperative kernel.  Each bucket round is two phases separated by bounded
-// grid barriers:
+// cooperative kernel.  One bucket round:
 //
-//   R (edgeMapData, Alg. 3 Update): for every arc (s, d, w) out of the
-//     current bucket F (all with D[s] = b): nDist = b + w; if nDist < D[d],
-//     priority-write (atomicMin) D[d]; the first successful writer of the
-//     round wins a test-and-set (a round stamp) and appends d to Moved.  The
-//     sparse form is the blocked edgeMap of §6.2; with dense_wbfs the round
-//     may instead pull: every vertex with D[v] > b + 1 takes the minimum of
-//     b + w over neighbours with D[u] = b (the dense switch of the SSSP
-//     experiments, "switch to a dense edgeMap once the frontiers are
-//     sufficiently dense").
-//   E (vertexMap(Moved, Reset) + updateBuckets + nextBucket): the next bucket
-//     id is the smallest of (the minimum distance written in R, the lowest
-//     non-empty open bucket, the overflow minimum); moved vertices are filed
-//     under their final distance, and the live entries of the next bucket
-//     (D[v] equal to the bucket id; stale ones are dropped) become the next
-//     frontier, compacted with its degree prefix for the blocked edgeMap.
+//   nextBucket: every CTA computes, from the bucket counters, the smallest
+//     bucket value b with unconsumed entries (identically in every CTA).
+//   edgeMapData (Alg. 3 Update): the live entries of bucket b (D[v] == b;
+//     entries whose distance dropped after they were filed are stale — lazy
+//     deletion) relax their arcs: nDist = b + w; if nDist < D[d], priority-
+//     write D[d] with atomicMin.  A successful write files d straight into
+//     the bucket of its new distance (Reset + updateBuckets of Alg. 3, done
+//     at the write instead of in a later vertexMap pass, so a round needs no
+//     Moved list and no test-and-set: a vertex lowered twice in a round
+//     leaves one stale entry behind).
+//       - vertices of degree <= heavy_cutoff / 8 are expanded by their warp: the warp's
+//         32 entries get a warp-local degree prefix and the warp walks their
+//         arcs 32 at a time (every lane busy, coalesced target loads);
+//       - heavier vertices are compacted into a frontier queue with a global
+//         degree prefix and expanded afterwards by the blocked edgeMap
+//         (§6.2) over all CTAs, so one hub is spread over the whole GPU.
+//   With dense_wbfs, a bucket with more than n / pull_divisor entries is
+//   instead pulled: every vertex with D[v] > b + 1 takes the minimum of b + w
+//   over neighbours with D[u] == b (the dense switch of the SSSP experiments).
 //
-// The bucket structure (Julienne's makeBuckets / nextBucket / updateBuckets,
-// INCREASING order) is a window of nB open buckets, bucket value x in slot
-// x mod nB, plus an overflow bucket for values beyond the window; when the
-// window runs dry the overflow is scanned and refilled into a window that
-// starts at its minimum.  With nB > max weight nothing ever overflows.
+// One bounded grid barrier per round, two when heavy vertices were found.
+//
+// Bucket structure (Julienne's makeBuckets / nextBucket / updateBuckets,
+// INCREASING order): nB open buckets, value x in slot x mod nB; each slot is
+// a ring buffer of n entries with a monotone append counter, and every CTA
+// keeps the consumed position of each slot in shared memory (all CTAs consume
+// identically).  A value has at most n entries (D only decreases), so a ring
+// never overwrites unconsumed entries.  If nB > max weight the window slides
+// to the current bucket and nothing overflows.  Otherwise the window is fixed
+// and values beyond it go to an overflow bucket, which refills a window
+// starting at its minimum once the open buckets run dry.
 #include <cuda_runtime.h>
 
 #include "dev_common.cuh"
@@ -35,11 +44,10 @@ struct WbfsParams {
   DevGraph g;
   int32_t src;
   int32_t *dist;
-  int32_t *stamp;
-  int32_t *moved[2];
   int32_t *slots;
   uint32_t *slot_cnt;
   int32_t nB;
+  int slide;
   int2 *ovf[2];
   uint32_t ovf_cap;
   int32_t *q;
@@ -47,95 +55,165 @@ struct WbfsParams {
   uint32_t *cs;
   uint32_t cs_cap;
   Ctl *ctl;
+  TraceRec *trace;
+  int trace_cap;
   int pull_divisor;
   int dense;
   int bmax;
+  int cap;
   int log2_bmax_fine;
-  int pull_serial;
+  int heavy;
   int inject_wait;
   long long cap_ns;
 };
 
 namespace {
 
-// Update of Alg. 3 (sparse direction).
+constexpr int kMaskWords = 8;  // pending / filed slot masks: nB <= 256
+
+struct Counters {
+  unsigned long long scanned, relax, inserts, expanded, heavy;
+};
+
+// Bucket filing, staged per CTA: lanes whose writeMin succeeded reserve a
+// place in the shared-memory stage (one shared atomic per warp); the CTA then
+// flushes the stage with one global atomicAdd per bucket slot touched, so
+// the few slot counters are not hammered once per warp.
+struct FileSink {
+  const WbfsParams *P;
+  int32_t lo;
+  int cur;
+  Counters *c;
+  unsigned *imask;   // this round's filed-slot mask (global)
+  unsigned *s_pub;   // slots this CTA already published this round
+
+  __device__ __forceinline__ void append(PushSmem &S, bool low, int32_t v, uint32_t ndu) {
+    const unsigned bal = __ballot_sync(kFull, low);
+    if (bal == 0) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(bal) - 1;
+    uint32_t pos = 0;
+    if (lane == leader) pos = atomicAdd(&S.misc[4], (uint32_t)__popc(bal));
+    pos = __shfl_sync(kFull, pos, leader);
+    if (low) {
+      const int32_t nd = (int32_t)ndu;
+      const uint32_t r = pos + __popc(bal & lanemask_lt());
+      S.fv[r] = v;
+      S.fs[r] = (P->slide || nd < lo + P->nB) ? nd % P->nB : -nd - 2;
+    }
+  }
+  __device__ __forceinline__ void step_done(PushSmem &S) {
+    __syncthreads();
+    if (S.misc[4] + kU * blockDim.x > S.cap_out) flush(S);
+  }
+  // CTA-collective.
+  __device__ void flush(PushSmem &S) {
+    __syncthreads();
+    const uint32_t k = S.misc[4];
+    if (k == 0) return;
+    const int nB = P->nB;
+    const uint32_t n = (uint32_t)P->g.n;
+    for (int i = threadIdx.x; i < nB; i += blockDim.x) S.hist[i] = 0u;
+    if (threadIdx.x == 0) {
+      S.misc[5] = 0u;
+      S.misc[7] = (uint32_t)kInf;
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < k; i += blockDim.x) {
+      const int32_t sl = S.fs[i];
+      if (sl >= 0) {
+        S.pref[i] = atomicAdd(&S.hist[sl], 1u);
+      } else {
+        S.pref[i] = atomicAdd(&S.misc[5], 1u);
+        atomicMin(&S.misc[7], (uint32_t)(-sl - 2));
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nB; i += blockDim.x) {
+      const uint32_t h = S.hist[i];
+      if (h) {
+        S.gbase[i] = atomicAdd(P->slot_cnt + i, h);
+        const unsigned bit = 1u << (i & 31);
+        if (!(s_pub[i >> 5] & bit)) {
+          atomicOr(s_pub + (i >> 5), bit);
+          atomicOr(imask + (i >> 5), bit);
+        }
+      }
+    }
+    if (threadIdx.x == 0 && S.misc[5]) {
+      S.misc[6] = atomicAdd(&P->ctl->ovf_cnt[cur], S.misc[5]);
+      atomicMin(&P->ctl->ovf_min[cur], (int)S.misc[7]);
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < k; i += blockDim.x) {
+      const int32_t sl = S.fs[i];
+      const int32_t v = S.fv[i];
+      if (sl >= 0) {
+        const uint32_t pos = (S.gbase[sl] + S.pref[i]) % n;
+        P->slots[(size_t)sl * n + pos] = v;
+      } else {
+        const uint32_t pos = S.misc[6] + S.pref[i];
+        if (pos < P->ovf_cap) P->ovf[cur][pos] = make_int2(v, -sl - 2);
+        else raise_error(P->ctl, GBF_ERR_OVERFLOW, 6);
+      }
+    }
+    if (threadIdx.x == 0) c->inserts += k;
+    __syncthreads();
+    if (threadIdx.x == 0) S.misc[4] = 0;
+    __syncthreads();
+  }
+};
+
+// Update of Alg. 3 for kU windows of arcs out of bucket b: all target and
+// weight loads, then the distance loads, then the writeMins.
 struct RelaxFn {
+  const int32_t *tgt;
   const uint32_t *w;
   int32_t *dist;
-  int32_t *stamp;
-  int32_t b, t;
-  int32_t gmin;
+  int32_t b;
   unsigned long long relax;
-  __device__ __forceinline__ void operator()(int32_t, int32_t v, uint32_t idx, bool &emit,
-                                             int32_t &ov, uint32_t &) {
-    const int32_t nd = b + (int32_t)__ldg(w + idx);
-    if (nd >= dist[v]) return;
-    const int32_t old = atomicMin(dist + v, nd);
-    if (old <= nd) return;
-    relax++;
-    gmin = min(gmin, nd);
-    if (atomicExch(stamp + v, t) != t) {
-      emit = true;
-      ov = v;
+  template <class Sink>
+  __device__ __forceinline__ void batch(const bool *val, const int32_t *, const uint32_t *idx,
+                                        Sink &sink, PushSmem &S) {
+    int32_t v[kU], nd[kU], dv[kU];
+#pragma unroll
+    for (int r = 0; r < kU; r++) {
+      v[r] = val[r] ? __ldg(tgt + idx[r]) : 0;
+      nd[r] = val[r] ? b + (int32_t)__ldg(w + idx[r]) : kInf;
+    }
+#pragma unroll
+    for (int r = 0; r < kU; r++) dv[r] = val[r] ? dist[v[r]] : kInf;
+    bool low[kU];
+#pragma unroll
+    for (int r = 0; r < kU; r++) {
+      low[r] = false;
+      if (nd[r] < dv[r]) low[r] = atomicMin(dist + v[r], nd[r]) > nd[r];
+    }
+#pragma unroll
+    for (int r = 0; r < kU; r++) {
+      if (low[r]) relax++;
+      sink.append(S, low[r], v[r], (uint32_t)nd[r]);
     }
   }
 };
 
-// Warp-aggregated append of (v) to bucket slot `slot` (lanes with slot < 0 skip).
-__device__ __forceinline__ void slot_insert(const WbfsParams &P, int32_t slot, int32_t v,
-                                            unsigned long long &inserts) {
-  const unsigned grp = __match_any_sync(kFull, slot);
-  if (slot < 0) return;
-  const int lane = threadIdx.x & 31;
-  const int leader = __ffs(grp) - 1;
-  uint32_t base = 0;
-  if (lane == leader) base = atomicAdd(P.slot_cnt + slot, (unsigned)__popc(grp));
-  base = __shfl_sync(grp, base, leader);
-  const uint32_t pos = base + __popc(grp & lanemask_lt());
-  if (pos < (uint32_t)P.g.n) P.slots[(size_t)slot * (size_t)P.g.n + pos] = v;
-  else raise_error(P.ctl, GBF_ERR_OVERFLOW, 5);
-  inserts++;
-}
-
-// Warp-aggregated append of (v, d) to overflow buffer `which`.
-__device__ __forceinline__ void ovf_insert(const WbfsParams &P, int which, bool ins, int32_t v,
-                                           int32_t d, unsigned long long &inserts) {
-  const unsigned bal = __ballot_sync(kFull, ins);
-  if (!bal) return;
-  const int lane = threadIdx.x & 31;
-  const int leader = __ffs(bal) - 1;
-  uint32_t base = 0;
-  if (lane == leader) base = atomicAdd(&P.ctl->ovf_cnt[which], (unsigned)__popc(bal));
-  base = __shfl_sync(kFull, base, leader);
-  if (ins) {
-    const uint32_t pos = base + __popc(bal & lanemask_lt());
-    if (pos < P.ovf_cap) {
-      P.ovf[which][pos] = make_int2(v, d);
-      atomicMin(&P.ctl->ovf_min[which], d);
-    } else {
-      raise_error(P.ctl, GBF_ERR_OVERFLOW, 6);
-    }
-    inserts++;
-  }
-}
-
-// Dense edgeMap for one bucket: pull the minimum of b + w over neighbours in
-// the bucket (D[u] == b) into every vertex with D[v] > b + 1.
-__device__ void dense_relax(const WbfsParams &P, int32_t b, int32_t t, int32_t &gmin,
-                            unsigned long long &relax, unsigned long long &scanned) {
+// Dense edgeMap for one bucket: owner-computes pull of min(b + w) over
+// neighbours with D[u] == b, into every vertex with D[v] > b + 1.  Word-
+// contiguous CTA ranges keep the loop CTA-uniform for the filing stage.
+__device__ void dense_round(const WbfsParams &P, int32_t b, PushSmem &S, FileSink &sink,
+                            Counters &c) {
   const DevGraph &g = P.g;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const uint32_t nwords = ((uint32_t)g.n + 31) >> 5;
-  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t tw = (gridDim.x * blockDim.x) >> 5;
-  int32_t *mlist = P.moved[t & 1];
-  unsigned int *mcount = &P.ctl->mcnt[t & 1];
-  for (uint32_t wi = gw; wi < nwords; wi += tw) {
+  const uint32_t per = (nwords + gridDim.x - 1) / gridDim.x;
+  const uint32_t wlo = min(nwords, blockIdx.x * per), whi = min(nwords, wlo + per);
+  for (uint32_t base = wlo; base < whi; base += nw) {
+    const uint32_t wi = base + warp;
     const int32_t v = (int32_t)(wi * 32 + lane);
     int32_t dv = kInf;
     uint32_t s = 0, e = 0;
     bool cand = false;
-    if (v < g.n) {
+    if (wi < whi && v < g.n) {
       dv = P.dist[v];
       if (dv > b + 1) {
         s = __ldg(g.off + v);
@@ -144,56 +222,54 @@ __device__ void dense_relax(const WbfsParams &P, int32_t b, int32_t t, int32_t &
       }
     }
     int32_t best = kInf;
-    uint32_t k = s;
-    if (cand) {
-      const uint32_t lim = min(e, s + (uint32_t)P.pull_serial);
-      for (; k < lim && best != b + 1; k++) {
-        const int32_t u = __ldg(g.tgt + k);
-        if (P.dist[u] == b) best = min(best, b + (int32_t)__ldg(g.w + k));
-      }
-      scanned += k - s;
-    }
-    unsigned rm = __ballot_sync(kFull, cand && best != b + 1 && k < e);
+    unsigned rm = __ballot_sync(kFull, cand);
+    // each candidate's list is scanned by the whole warp, 32 arcs at a time,
+    // stopping once the lower bound b + 1 is reached
     while (rm) {
       const int l = __ffs(rm) - 1;
       rm &= rm - 1;
-      const uint32_t ks = __shfl_sync(kFull, k, l), ke = __shfl_sync(kFull, e, l);
-      int32_t wb = __shfl_sync(kFull, best, l);
-      uint32_t looked = 0;
-      for (uint32_t c = ks; c < ke && wb != b + 1; c += 32) {
-        const uint32_t kk = c + lane;
-        int32_t cand_d = kInf;
+      const uint32_t ks = __shfl_sync(kFull, s, l), ke = __shfl_sync(kFull, e, l);
+      int32_t wb = kInf;
+      for (uint32_t k0 = ks; k0 < ke && wb != b + 1; k0 += 32) {
+        const uint32_t kk = k0 + lane;
+        int32_t cd = kInf;
         if (kk < ke) {
           const int32_t u = __ldg(g.tgt + kk);
-          if (P.dist[u] == b) cand_d = b + (int32_t)__ldg(g.w + kk);
+          if (P.dist[u] == b) cd = b + (int32_t)__ldg(g.w + kk);
         }
-        wb = min(wb, __reduce_min_sync(kFull, cand_d));
-        looked += min(32u, ke - c);
+        wb = min(wb, (int32_t)__reduce_min_sync(kFull, cd));
+        if (lane == 0) c.scanned += min(32u, ke - k0);
       }
-      if (lane == l) {
-        best = wb;
-        scanned += looked;
-      }
+      if (lane == l) best = wb;
     }
     const bool low = cand && best < dv;
     if (low) {
       P.dist[v] = best;
-      relax++;
-      gmin = min(gmin, best);
+      c.relax++;
     }
-    const unsigned bal = __ballot_sync(kFull, low);
-    if (bal) {
-      const int leader = __ffs(bal) - 1;
-      uint32_t pos = 0;
-      if (lane == leader) pos = atomicAdd(mcount, (unsigned)__popc(bal));
-      pos = __shfl_sync(kFull, pos, leader);
-      if (low) {
-        const uint32_t r = pos + __popc(bal & lanemask_lt());
-        if (r < (uint32_t)g.n) mlist[r] = v;
-        else raise_error(P.ctl, GBF_ERR_OVERFLOW, 7);
-      }
+    sink.append(S, low, v, (uint32_t)best);
+    sink.step_done(S);
+  }
+  sink.flush(S);
+}
+
+// nextBucket from the CTA's pending-slot set (identical in every CTA): the
+// smallest value among slots marked pending, or kInf.  Values of the window
+// [lo, lo + nB) map one-to-one to slots.
+__device__ int32_t next_bucket(const unsigned *s_pend, int nB, int32_t lo, int *s_tmp) {
+  int32_t best = kInf;
+  for (int i = threadIdx.x; i < nB; i += blockDim.x) {
+    if ((s_pend[i >> 5] >> (i & 31)) & 1u) {
+      const int32_t rel = ((i - lo % nB) % nB + nB) % nB;
+      best = min(best, lo + rel);
     }
   }
+  best = block_min_i32(best, s_tmp);
+  if (threadIdx.x == 0) s_tmp[32] = best;
+  __syncthreads();
+  best = s_tmp[32];
+  __syncthreads();
+  return best;
 }
 
 }  // namespace
@@ -202,198 +278,193 @@ __global__ void __launch_bounds__(1024) wbfs_kernel(WbfsParams P) {
   extern __shared__ unsigned long long smem_raw[];
   __shared__ int s_flag;
   __shared__ int s_int[40];
-  PushSmem S = carve_push_smem(smem_raw, P.bmax);
-  if (threadIdx.x == 0) S.misc[0] = 0;
+  __shared__ unsigned s_pend[kMaskWords];  // slots with unconsumed entries
+  __shared__ unsigned s_pub[kMaskWords];   // slots this CTA already published this round
+  const int nB = P.nB;
+  const SmemShape sh{P.bmax, P.cap, 1, nB};
+  PushSmem S = carve_push_smem(smem_raw, sh);
+  uint32_t *s_base = (uint32_t *)((char *)smem_raw + push_smem_bytes(sh));
+  for (int i = threadIdx.x; i < nB; i += blockDim.x) s_base[i] = 0u;
+  for (int i = threadIdx.x; i < kMaskWords; i += blockDim.x) {
+    s_pend[i] = (i == 0) ? 1u : 0u;  // the source sits in slot 0
+    s_pub[i] = 0u;
+  }
+  if (threadIdx.x == 0) {
+    S.misc[0] = 0;
+    S.misc[4] = 0;
+  }
   Ctl *ctl = P.ctl;
   Barrier bar{0u, P.cap_ns};
   const DevGraph g = P.g;
   const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
-  const int32_t src = P.src, nB = P.nB;
-  unsigned long long scanned = 0, relax = 0, inserts = 0, expanded = 0;
+  const int32_t src = P.src;
+  Counters c{0, 0, 0, 0, 0};
+  const unsigned long long t_start = globaltimer();
 
-  // makeBuckets: D = inf except D[src] = 0; only src in bucket 0.
-  for (uint32_t i = gt; i < (uint32_t)g.n; i += gs) {
-    P.dist[i] = (i == (uint32_t)src) ? 0 : kInf;
-    P.stamp[i] = 0;
-  }
+  // makeBuckets: D = inf except D[src] = 0; src filed in bucket 0.
+  for (uint32_t i = gt; i < (uint32_t)g.n; i += gs) P.dist[i] = (i == (uint32_t)src) ? 0 : kInf;
   if (blockIdx.x == 0) {
-    for (int i = threadIdx.x; i < nB; i += blockDim.x) P.slot_cnt[i] = 0u;
-    const uint32_t d0 = __ldg(g.off + src + 1) - __ldg(g.off + src);
+    for (int i = threadIdx.x; i < nB; i += blockDim.x) P.slot_cnt[i] = (i == 0) ? 1u : 0u;
     if (threadIdx.x == 0) {
-      ctl->gmin[0] = kInf;
-      ctl->gmin[1] = kInf;
+      P.slots[0] = src;
       ctl->ovf_min[0] = kInf;
       ctl->ovf_min[1] = kInf;
-      if (d0 > 0) {
-        P.q[0] = src;
-        P.qoff[0] = 0;
-        st_vol(ctl->fr[0], (1ull << 32) | d0);
-      }
     }
-    for (uint32_t c = threadIdx.x; c < (d0 + kFine - 1) / kFine; c += blockDim.x)
-      if (c < P.cs_cap) P.cs[c] = 0;
   }
   if (P.inject_wait && blockIdx.x == 0 && threadIdx.x == 0) injected_wait(ctl, P.cap_ns);
   __syncthreads();
   bool ok = grid_sync(ctl, bar, &s_flag);
 
-  int32_t b = 0, lo = 0;
-  int cur = 0;  // active overflow buffer
+  int32_t lo = 0;
+  int cur = 0;         // active overflow buffer
+  int32_t prev = -1;   // slot consumed by the previous round (-1: none)
   for (int32_t t = 1; ok; t++) {
-    // ---------------- R phase: relax the frontier of bucket b
-    const unsigned long long fr = ld_vol(ctl->fr[(t - 1) & 1]);
-    const uint32_t cnt = (uint32_t)(fr >> 32), D = (uint32_t)fr;
-    // Snapshot the bucket state for the next nextBucket decision now: the
-    // open buckets and the overflow bucket only change in E phases, so every
-    // CTA sees the same values here.  The slot of the bucket just extracted
-    // (value b) is skipped: it is being emptied.
-    int32_t smin = kInf;
-    for (int i = threadIdx.x; i < nB; i += blockDim.x) {
-      if (i != b % nB && ld_vol(P.slot_cnt[i]) > 0u) {
-        const int32_t rel = ((i - lo % nB) % nB + nB) % nB;
-        smin = min(smin, lo + rel);
-      }
+    // ---------------- nextBucket.  Pending slots: those of the last round
+    // minus the one it consumed, plus every slot filed into during it (the
+    // masks of round t-1 are complete: a grid barrier separates the rounds).
+    // Fast CTAs already filing in round t write mask t % 3, read by nobody yet.
+    unsigned *imask = ctl->imask[t % 3];
+    if (threadIdx.x < kMaskWords) {
+      unsigned pm = s_pend[threadIdx.x];
+      if (prev >= 0 && (prev >> 5) == (int)threadIdx.x) pm &= ~(1u << (prev & 31));
+      if (t > 1) pm |= ld_vol(ctl->imask[(t - 1) % 3][threadIdx.x]);
+      s_pend[threadIdx.x] = pm;
+      s_pub[threadIdx.x] = 0u;
     }
-    smin = block_min_i32(smin, s_int);
-    if (threadIdx.x == 0) s_int[32] = smin;
     __syncthreads();
-    smin = s_int[32];
-    const uint32_t oc = ld_vol(ctl->ovf_cnt[cur]);
-    const int32_t om = oc ? ld_vol(ctl->ovf_min[cur]) : kInf;
-    __syncthreads();
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      st_vol(ctl->mcnt[(t + 1) & 1], 0u);
-      st_vol(ctl->gmin[(t + 1) & 1], kInf);
-      st_vol(ctl->fr[t & 1], 0ull);
-      if (t > 1) st_vol(P.slot_cnt[b % nB], 0u);
-      st_vol(ctl->ovf_cnt[cur ^ 1], 0u);
-      st_vol(ctl->ovf_min[cur ^ 1], kInf);
-      atomicAdd(&ctl->rounds, 1);
-    }
-    int32_t gmin = kInf;
-    if (cnt > 0) {
-      const bool dense = P.dense && P.pull_divisor > 0 &&
-                         (unsigned long long)D * (unsigned)P.pull_divisor > g.m;
-      if (blockIdx.x == 0 && threadIdx.x == 0) {
-        atomicAdd(dense ? &ctl->pull_rounds : &ctl->push_rounds, 1);
-        if (!dense) {
-          scanned += D;
-          expanded += cnt;
-        }
-      }
-      if (dense) {
-        dense_relax(P, b, t, gmin, relax, scanned);
-      } else {
-        QueueIn in{P.q, P.qoff, P.cs, cnt, D};
-        RelaxFn fn{g.w, P.dist, P.stamp, b, t, kInf, 0};
-        ListSink sink{P.moved[t & 1], &ctl->mcnt[t & 1], (uint32_t)g.n, ctl};
-        blocked_edge_map(g, in, chunk_shift(D, P.log2_bmax_fine), S, fn, sink, ctl);
-        gmin = fn.gmin;
-        relax += fn.relax;
-      }
-    }
-    {
-      const int m = block_min_i32(gmin, s_int);
-      if (threadIdx.x == 0 && m != kInf) atomicMin(&ctl->gmin[t & 1], m);
-    }
-    if (!grid_sync(ctl, bar, &s_flag)) break;
-
-    // ---------------- E phase: Reset + updateBuckets + nextBucket
-    const int32_t gm = ld_vol(ctl->gmin[t & 1]);
-    const uint32_t mc = min(ld_vol(ctl->mcnt[t & 1]), (uint32_t)g.n);
-    const int32_t bn = min(gm, min(smin, om));
-    if (bn == kInf) break;  // nextBucket returned nullbkt
-    const bool refill = oc > 0 && bn >= lo + nB;
-    const int32_t lo_new = (oc == 0 || refill) ? bn : lo;
-    const int32_t *mlist = P.moved[t & 1];
-    QueueOut fout{P.q, P.qoff, P.cs, &ctl->fr[t & 1], (uint32_t)g.n, P.cs_cap};
-    const uint32_t stride = gridDim.x * blockDim.x;
-    const uint32_t wbase = gt & ~31u;  // warp-uniform loop start
-
-    if (refill) {
-      // Refill the window [bn, bn + nB) from the overflow bucket (stale
-      // entries dropped), then file Moved under the new window.
-      const uint32_t ocap = min(oc, P.ovf_cap);
-      for (uint32_t base = wbase; base < ocap; base += stride) {
-        const uint32_t i = base + (threadIdx.x & 31);
-        const bool valid = i < ocap;
+    if (blockIdx.x == 0 && threadIdx.x < kMaskWords) st_vol(ctl->imask[(t + 1) % 3][threadIdx.x], 0u);
+    if (blockIdx.x == 0 && threadIdx.x == 0) st_vol(ctl->fr[(t + 1) % 3], 0ull);
+    const int32_t b = next_bucket(s_pend, nB, lo, s_int);
+    if (b == kInf) {
+      // open buckets are dry: refill from the overflow bucket, or finish
+      const uint32_t oc = min(ld_vol(ctl->ovf_cnt[cur]), P.ovf_cap);
+      if (P.slide || oc == 0) break;
+      const int32_t nlo = ld_vol(ctl->ovf_min[cur]);
+      if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&ctl->refills, 1);
+      // into the new window [nlo, nlo + nB), the rest into the other buffer
+      FileSink fs{&P, nlo, cur ^ 1, &c, imask, s_pub};
+      for (uint32_t base = blockIdx.x * blockDim.x; base < oc; base += gs) {
+        const uint32_t i = base + threadIdx.x;
+        const bool valid = i < oc;
         const int2 e = valid ? P.ovf[cur][i] : make_int2(0, 0);
         const bool live = valid && P.dist[e.x] == e.y;
-        const bool into_slot = live && e.y < lo_new + nB;
-        slot_insert(P, into_slot ? (e.y % nB) : -1, e.x, inserts);
-        ovf_insert(P, cur ^ 1, live && !into_slot, e.x, e.y, inserts);
+        fs.append(S, live, e.x, (uint32_t)e.y);
+        fs.step_done(S);
       }
-      for (uint32_t base = wbase; base < mc; base += stride) {
-        const uint32_t i = base + (threadIdx.x & 31);
-        const bool valid = i < mc;
-        const int32_t v = valid ? mlist[i] : 0;
-        const int32_t d = valid ? P.dist[v] : kInf;
-        const bool keep = valid && (__ldg(g.off + v + 1) - __ldg(g.off + v)) >= 2u;
-        const bool into_slot = keep && d < lo_new + nB;
-        slot_insert(P, into_slot ? (d % nB) : -1, v, inserts);
-        ovf_insert(P, cur ^ 1, keep && !into_slot, v, d, inserts);
-      }
-      if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&ctl->refills, 1);
+      fs.flush(S);
+      lo = nlo;
+      prev = -1;
       if (!grid_sync(ctl, bar, &s_flag)) break;
+      // the scanned buffer is consumed; the other one holds the remainder
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st_vol(ctl->ovf_cnt[cur], 0u);
+        st_vol(ctl->ovf_min[cur], kInf);
+      }
       cur ^= 1;
-    } else {
-      // File Moved: members of the next bucket go straight to the frontier.
-      for (uint32_t base = blockIdx.x * blockDim.x; base < mc; base += stride) {
-        const uint32_t i = base + threadIdx.x;
-        const bool valid = i < mc;
-        const int32_t v = valid ? mlist[i] : 0;
-        const int32_t d = valid ? P.dist[v] : kInf;
-        const uint32_t deg = valid ? (__ldg(g.off + v + 1) - __ldg(g.off + v)) : 0u;
-        const bool keep = valid && deg >= 2u;
-        const bool to_f = keep && d == bn;
-        const bool into_slot = keep && !to_f && d < lo_new + nB;
-        const bool into_ovf = keep && !to_f && !into_slot;
-        slot_insert(P, into_slot ? (d % nB) : -1, v, inserts);
-        ovf_insert(P, cur, into_ovf, v, d, inserts);
-        stage_append(S, to_f, v, deg);
-        __syncthreads();
-        if (S.misc[0] + blockDim.x > S.cap_out) stage_flush(S, fout, ctl);
-      }
+      if (!grid_sync(ctl, bar, &s_flag)) break;
+      continue;
     }
-    // Extract the live entries of bucket bn; entries whose distance changed
-    // after they were filed are stale and dropped (lazy deletion).
-    {
-      const int32_t slot = bn % nB;
-      const uint32_t scnt = min(ld_vol(P.slot_cnt[slot]), (uint32_t)g.n);
-      const int32_t *sl = P.slots + (size_t)slot * (size_t)g.n;
-      for (uint32_t base = blockIdx.x * blockDim.x; base < scnt; base += stride) {
-        const uint32_t i = base + threadIdx.x;
-        bool live = false;
-        int32_t v = 0;
-        uint32_t deg = 0;
-        if (i < scnt) {
-          v = sl[i];
-          if (P.dist[v] == bn) {
-            deg = __ldg(g.off + v + 1) - __ldg(g.off + v);
-            live = deg >= 2u;
-          }
+    if (P.slide) lo = b;
+    const int sb = b % nB;
+    prev = sb;
+    // No CTA files into slot sb during this round (its values differ from b
+    // by less than nB), so its counter is stable here.
+    const uint32_t rb = s_base[sb];
+    const uint32_t cntb = min(ld_vol(P.slot_cnt[sb]) - rb, (uint32_t)g.n);
+    __syncthreads();
+    if (threadIdx.x == 0) s_base[sb] = rb + cntb;
+    __syncthreads();
+    unsigned long long *fctr = &ctl->fr[t % 3];
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&ctl->rounds, 1);
+    FileSink fsink{&P, lo, cur, &c, imask, s_pub};
+    const bool dense = P.dense && P.pull_divisor > 0 &&
+                       (unsigned long long)cntb * (unsigned)P.pull_divisor > (unsigned long long)g.n;
+    if (dense) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&ctl->pull_rounds, 1);
+      dense_round(P, b, S, fsink, c);
+      if (!grid_sync(ctl, bar, &s_flag)) break;
+      if (P.trace && blockIdx.x == 0 && threadIdx.x == 0 && t <= P.trace_cap)
+        P.trace[t - 1] = TraceRec{t, 2, cntb, 0u, (long long)(globaltimer() - t_start), 0};
+      continue;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&ctl->push_rounds, 1);
+    // ---------------- edgeMapData over the live entries of bucket b
+    QueueOut fout{P.q, P.qoff, P.cs, fctr, (uint32_t)g.n, P.cs_cap};
+    RelaxFn fn{g.tgt, g.w, P.dist, b, 0};
+    const int32_t *sl = P.slots + (size_t)sb * (size_t)g.n;
+    for (uint32_t it = blockIdx.x * blockDim.x; it < cntb; it += gs) {
+      const uint32_t i = it + threadIdx.x;
+      int32_t v = 0;
+      bool live = false;
+      uint32_t a0 = 0, deg = 0;
+      if (i < cntb) {
+        v = sl[(rb + i) % (uint32_t)g.n];
+        if (P.dist[v] == b) {
+          a0 = __ldg(g.off + v);
+          deg = __ldg(g.off + v + 1) - a0;
+          // a degree-1 vertex other than the source was reached from its only
+          // neighbour, which it cannot improve
+          live = deg >= 2u || (deg == 1u && v == src);
         }
-        stage_append(S, live, v, deg);
-        __syncthreads();
-        if (S.misc[0] + blockDim.x > S.cap_out) stage_flush(S, fout, ctl);
       }
+      const bool heavy = live && deg > (uint32_t)P.heavy;
+      stage_append(S, heavy, v, deg);
+      const bool light = live && !heavy;
+      if (live) c.expanded++;
+      if (heavy) c.heavy++;
+      // CTA-local degree prefix of the light entries (count in the high bits)
+      uint32_t tot;
+      const uint32_t ex = block_excl_scan(light ? ((1u << 20) | deg) : 0u, S.misc + 8, &tot);
+      if (light) {
+        const uint32_t j = ex >> 20;
+        S.base[j] = ex & 0xfffffu;
+        S.u[j] = v;
+        S.adj[j] = a0;
+      }
+      const uint32_t nv = tot >> 20, E = tot & 0xfffffu;
+      if (threadIdx.x == 0) {
+        S.base[nv] = E;
+        c.scanned += E;
+      }
+      __syncthreads();
+      walk_chunk(S, g.m, nv, 0u, E, fn, fsink);
+      if (S.misc[0] + blockDim.x > S.cap_out) stage_flush(S, fout, ctl);
     }
     stage_flush(S, fout, ctl);
-    lo = lo_new;
-    b = bn;
+    fsink.flush(S);
     if (!grid_sync(ctl, bar, &s_flag)) break;
+    // heavy-vertex counter of this round (triple-buffered: the slot zeroed by
+    // CTA 0 in round t + 1 is (t + 2) % 3, never this one)
+    const unsigned long long fr = ld_vol(*fctr);
+    const uint32_t hcnt = (uint32_t)(fr >> 32), hD = (uint32_t)fr;
+    const long long t_mid = (long long)(globaltimer() - t_start);
+    if (hcnt > 0) {
+      // heavy vertices of the bucket: blocked edgeMap over all CTAs
+      QueueIn in{P.q, P.qoff, P.cs, hcnt, hD};
+      // every heavy vertex has more than P.heavy edges
+      blocked_edge_map(g, in, chunk_shift(hD, (uint32_t)P.bmax, (uint32_t)P.heavy + 1u),
+                       (uint32_t)P.bmax, S, fn, fsink, ctl);
+      fsink.flush(S);
+      if (blockIdx.x == 0 && threadIdx.x == 0) c.scanned += hD;
+      if (!grid_sync(ctl, bar, &s_flag)) break;
+    }
+    c.relax += fn.relax;
+    if (P.trace && blockIdx.x == 0 && threadIdx.x == 0 && t <= P.trace_cap)
+      P.trace[t - 1] = TraceRec{t, hcnt ? 3 : 1, cntb, hD, (long long)(globaltimer() - t_start),
+                                hcnt ? t_mid : 0};
   }
-  // statistics: reached vertices are counted by the host from dist.
+  // statistics
   unsigned long long tt;
-  tt = block_sum64(scanned, S.misc64);
+  tt = block_sum64(c.scanned, S.misc64);
   if (threadIdx.x == 0 && tt) atomicAdd(&ctl->edges_scanned, tt);
-  tt = block_sum64(relax, S.misc64);
+  tt = block_sum64(c.relax, S.misc64);
   if (threadIdx.x == 0 && tt) atomicAdd(&ctl->relax, tt);
-  tt = block_sum64(inserts, S.misc64);
+  tt = block_sum64(c.inserts, S.misc64);
   if (threadIdx.x == 0 && tt) atomicAdd(&ctl->inserts, tt);
-  tt = block_sum64(expanded, S.misc64);
+  tt = block_sum64(c.expanded, S.misc64);
   if (threadIdx.x == 0 && tt) atomicAdd(&ctl->expanded, tt);
-
+  tt = block_sum64(c.heavy, S.misc64);
+  if (threadIdx.x == 0 && tt) atomicAdd(&ctl->heavy, tt);
 }
 
 gbf_status launch_wbfs(Graph &g, Workspace &ws, int32_t src, int32_t *dist, const Opts &o,
@@ -402,12 +473,10 @@ gbf_status launch_wbfs(Graph &g, Workspace &ws, int32_t src, int32_t *dist, cons
   P.g = g.dev();
   P.src = src;
   P.dist = dist;
-  P.stamp = ws.stamp;
-  P.moved[0] = ws.moved[0];
-  P.moved[1] = ws.moved[1];
   P.slots = ws.slots;
   P.slot_cnt = ws.slot_cnt;
   P.nB = ws.nB;
+  P.slide = (uint32_t)ws.nB > g.w_max ? 1 : 0;
   P.ovf[0] = ws.ovf[0];
   P.ovf[1] = ws.ovf[1];
   P.ovf_cap = (uint32_t)ws.ovf_cap;
@@ -416,16 +485,21 @@ gbf_status launch_wbfs(Graph &g, Workspace &ws, int32_t src, int32_t *dist, cons
   P.cs = ws.cs[0];
   P.cs_cap = (uint32_t)(((uint64_t)g.m + kFine - 1) / kFine + 2);
   P.ctl = ws.ctl;
+  P.trace = ws.trace;
+  P.trace_cap = ws.trace_cap;
   P.pull_divisor = o.pull_divisor;
   P.dense = o.dense_wbfs;
   P.bmax = o.heavy_cutoff;
+  P.cap = 2 * kU * o.block;
   int l = 0;
   while ((kFine << l) < (uint32_t)o.heavy_cutoff) l++;
   P.log2_bmax_fine = l;
-  P.pull_serial = o.pull_serial;
+  // vertices with more arcs than this go through the blocked edgeMap pass
+  P.heavy = o.heavy_cutoff / 8 > 32 ? o.heavy_cutoff / 8 : 32;
   P.inject_wait = o.inject_wait;
   P.cap_ns = o.spin_cap_ns;
-  const size_t smem = push_smem_bytes(o.heavy_cutoff);
+  const size_t smem =
+      push_smem_bytes(SmemShape{P.bmax, P.cap, 1, ws.nB}) + sizeof(uint32_t) * (size_t)ws.nB;
   GBF_CUDA(cudaFuncSetAttribute(wbfs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem));
   int per_sm = 0;
@@ -437,6 +511,7 @@ gbf_status launch_wbfs(Graph &g, Workspace &ws, int32_t src, int32_t *dist, cons
   int grid = per_sm * g.num_sms;
   if (o.ctas > 0 && o.ctas < grid) grid = o.ctas;
   GBF_CUDA(cudaMemsetAsync(ws.ctl, 0, sizeof(Ctl), st));
+  if (ws.trace) GBF_CUDA(cudaMemsetAsync(ws.trace, 0, sizeof(TraceRec) * (size_t)ws.trace_cap, st));
   void *args[] = {&P};
   GBF_CUDA(cudaLaunchCooperativeKernel((const void *)wbfs_kernel, dim3(grid), dim3(o.block), args,
                                        smem, st));

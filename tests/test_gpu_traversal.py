@@ -235,3 +235,19 @@ def test_device_buffers_and_streams(gb):
     gb.gbf_wait(h, st)
     assert np.array_equal(dist.cpu().numpy(), oracle.dijkstra(csr, s))
     gb.gbf_graph_destroy(h)
+
+
+def test_round_trace(gb):
+    csr = G.add_weights(G.rmat(14, 16, seed=12), 1, 22, seed=13)
+    g = gb.Graph(csr)
+    s = int(G.sources(csr, 1, seed=14)[0])
+    d, _ = g.bfs(s)
+    tr = gb.gbf_trace(g.h)
+    st = g.stats()
+    assert len(tr) == st["rounds"] and len(tr) >= int(d[d != INF].max())
+    assert [r[0] for r in tr] == list(range(1, len(tr) + 1))
+    assert all(b[4] >= a[4] for a, b in zip(tr, tr[1:]))
+    assert {r[1] for r in tr} <= {1, 2}
+    g.wbfs(s)
+    tr = gb.gbf_trace(g.h)
+    assert len(tr) == g.stats()["rounds"] > 0
