@@ -185,6 +185,21 @@ gbf_status gbf_wbfs(gbf_graph *g, int32_t src, int32_t *dist, int mem, const gbf
  */
 gbf_status gbf_wait(gbf_graph *g, void *cuda_stream, gbf_stats *stats);
 
+/*
+ * gbf_msbfs — k independent BFSs (1 <= k <= 64) from srcs[0..k) in one
+ * persistent launch, one bit lane of a uint64 per source per vertex
+ * (multi-source BFS; the paper's nearest precedent is the simultaneous
+ * searches from many centres of its SCC algorithm, §5 "Strongly Connected
+ * Components").  Each level is one edgeMap (§3) shared by all lanes.  The
+ * launch is captured once into a CUDA graph per set of knobs and replayed.
+ *   srcs  int32[k] in host memory (duplicates allowed)
+ *   dist  int32[k*n], row i = hop distances from srcs[i] (GBF_INF if unreachable)
+ *   mem   where dist lives; GBF_HOST blocks, GBF_DEVICE is stream-ordered
+ * Errors: GBF_ERR_INVALID for k out of range, a bad source or NULL pointers.
+ */
+gbf_status gbf_msbfs(gbf_graph *g, const int32_t *srcs, int32_t k, int32_t *dist, int mem,
+                     const gbf_options *opt, void *cuda_stream);
+
 /* One record per round of the last query (see gbf_trace). */
 typedef struct {
   int32_t round;          /* 1-based round (BFS level or wBFS bucket round) */

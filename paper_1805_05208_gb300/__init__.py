@@ -84,6 +84,7 @@ def _load() -> ctypes.CDLL:
         "gbf_bfs": (S, [P, I32, P, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
         "gbf_wbfs": (S, [P, I32, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
         "gbf_wait": (S, [P, P, ctypes.POINTER(gbf_stats)]),
+        "gbf_msbfs": (S, [P, P, I32, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
         "gbf_trace": (S, [P, ctypes.POINTER(gbf_round_trace), I32, ctypes.POINTER(I32)]),
         "gbf_bfs_noalloc": (S, [I32, U32, P, P, I32, P, P, ctypes.POINTER(gbf_options), P]),
     }
@@ -196,6 +197,14 @@ def gbf_wbfs(h: int, src: int, dist, opt: Optional[gbf_options] = None, stream=N
     _check(_lib.gbf_wbfs(h, int(src), pd, mem, _opt(opt), _stream(stream)), "gbf_wbfs")
 
 
+def gbf_msbfs(h: int, srcs, dist, opt: Optional[gbf_options] = None, stream=None) -> None:
+    """Multi-source BFS from k <= 64 sources into dist[k, n] (row i = source i)."""
+    s = np.ascontiguousarray(np.asarray(srcs, dtype=np.int32))
+    pd, mem = _ptr(dist)
+    _check(_lib.gbf_msbfs(h, s.ctypes.data, int(s.size), pd, mem, _opt(opt), _stream(stream)),
+           "gbf_msbfs")
+
+
 def gbf_wait(h: int, stream=None) -> dict:
     """Synchronise and return the statistics of the last device-memory query."""
     s = gbf_stats()
@@ -261,6 +270,11 @@ class Graph:
         p = np.empty(self.n, dtype=np.int32) if parents else None
         gbf_bfs(self.h, src, d, p, opt)
         return d, p
+
+    def msbfs(self, srcs, opt=None):
+        d = np.empty((len(srcs), self.n), dtype=np.int32)
+        gbf_msbfs(self.h, srcs, d, opt)
+        return d
 
     def wbfs(self, src: int, opt=None):
         d = np.empty(self.n, dtype=np.int32)

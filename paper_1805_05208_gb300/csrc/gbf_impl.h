@@ -89,13 +89,20 @@ struct Workspace {
   int32_t nB = 0;
   int2 *ovf[2] = {nullptr, nullptr};
   uint64_t ovf_cap = 0;
-  // MS-BFS (lazy)
+  // MS-BFS (lazy); queues 0 and 1 are shared with q/qoff/cs above
   unsigned long long *ms_seen = nullptr, *ms_visit = nullptr, *ms_next = nullptr;
-  int32_t *ms_dist_tmp = nullptr;   // 64*n for host outputs
-  int32_t *ms_srcs = nullptr;       // 64 device
-  int32_t *ms_srcs_host = nullptr;  // pinned 64
+  int32_t *ms_q[3] = {nullptr, nullptr, nullptr};
+  uint32_t *ms_qoff[3] = {nullptr, nullptr, nullptr};
+  uint32_t *ms_cs[3] = {nullptr, nullptr, nullptr};
+  int32_t *ms_touched = nullptr;
+  void *ms_call = nullptr;        // device parameter block
+  void *ms_call_host = nullptr;   // pinned staging of the parameter block
+  int32_t *ms_dist_tmp = nullptr; // 64*n, only for host-memory outputs
+  cudaStream_t ms_stream = nullptr;
+  cudaEvent_t ms_ready = nullptr, ms_done = nullptr;
   cudaGraphExec_t ms_exec = nullptr;
-  const void *ms_exec_key[4] = {nullptr, nullptr, nullptr, nullptr};
+  long long ms_key[6] = {0, 0, 0, 0, 0, 0};
+  int ms_grid = 0;
   // pinned host copy of the control block
   Ctl *ctl_host = nullptr;
   int last_kind = 0;   // 1 bfs, 2 wbfs, 3 msbfs

@@ -223,15 +223,51 @@ gbf_status ws_ensure_wbfs(Graph &g, Workspace &ws, int nB) {
   return GBF_OK;
 }
 
+gbf_status ws_ensure_msbfs(Graph &g, Workspace &ws, bool host_out) {
+  GBF_TRY(ws_ensure_base(g, ws));
+  const size_t n = (size_t)g.n;
+  const size_t cs = ((size_t)g.m + dev::kFine - 1) / dev::kFine + 2;
+  size_t acc = 0;
+  if (!ws.ms_seen) {
+    GBF_TRY(dmalloc(&ws.ms_seen, n, acc));
+    GBF_TRY(dmalloc(&ws.ms_visit, 2 * n, acc));
+    GBF_TRY(dmalloc(&ws.ms_next, n, acc));
+    GBF_TRY(dmalloc(&ws.ms_q[2], n, acc));
+    GBF_TRY(dmalloc(&ws.ms_qoff[2], n, acc));
+    GBF_TRY(dmalloc(&ws.ms_cs[2], cs, acc));
+    GBF_TRY(dmalloc(&ws.ms_touched, n, acc));
+    char *call = nullptr;
+    GBF_TRY(dmalloc(&call, 512, acc));
+    ws.ms_call = call;
+    for (int i = 0; i < 2; i++) {
+      ws.ms_q[i] = ws.q[i];
+      ws.ms_qoff[i] = ws.qoff[i];
+      ws.ms_cs[i] = ws.cs[i];
+    }
+    GBF_CUDA(cudaMallocHost(&ws.ms_call_host, 512));
+    GBF_CUDA(cudaStreamCreateWithFlags(&ws.ms_stream, cudaStreamNonBlocking));
+    GBF_CUDA(cudaEventCreateWithFlags(&ws.ms_ready, cudaEventDisableTiming));
+    GBF_CUDA(cudaEventCreateWithFlags(&ws.ms_done, cudaEventDisableTiming));
+  }
+  if (host_out && !ws.ms_dist_tmp) GBF_TRY(dmalloc(&ws.ms_dist_tmp, 64 * n, acc));
+  ws.bytes += acc;
+  return GBF_OK;
+}
+
 void ws_free(Workspace &ws) {
   void *ptrs[] = {ws.visited, ws.fbm[0], ws.fbm[1], ws.q[0], ws.q[1], ws.qoff[0], ws.qoff[1],
-                  ws.cs[0], ws.cs[1], ws.ctl, ws.dist_tmp, ws.parent_tmp, ws.trace, ws.slots, ws.slot_cnt, ws.ovf[0], ws.ovf[1], ws.ms_seen,
-                  ws.ms_visit, ws.ms_next, ws.ms_dist_tmp, ws.ms_srcs};
+                  ws.cs[0], ws.cs[1], ws.ctl, ws.dist_tmp, ws.parent_tmp, ws.trace, ws.slots,
+                  ws.slot_cnt, ws.ovf[0], ws.ovf[1], ws.ms_seen, ws.ms_visit, ws.ms_next,
+                  ws.ms_q[2], ws.ms_qoff[2], ws.ms_cs[2], ws.ms_touched, ws.ms_call,
+                  ws.ms_dist_tmp};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (ws.ctl_host) cudaFreeHost(ws.ctl_host);
-  if (ws.ms_srcs_host) cudaFreeHost(ws.ms_srcs_host);
+  if (ws.ms_call_host) cudaFreeHost(ws.ms_call_host);
   if (ws.ms_exec) cudaGraphExecDestroy(ws.ms_exec);
+  if (ws.ms_ready) cudaEventDestroy(ws.ms_ready);
+  if (ws.ms_done) cudaEventDestroy(ws.ms_done);
+  if (ws.ms_stream) cudaStreamDestroy(ws.ms_stream);
   ws = Workspace();
 }
 
@@ -471,6 +507,26 @@ gbf_status gbf_trace(gbf_graph *h, gbf_round_trace *out, int32_t cap, int32_t *c
   }
   *count = k;
   return GBF_OK;
+}
+
+gbf_status gbf_msbfs(gbf_graph *h, const int32_t *srcs, int32_t k, int32_t *dist, int mem,
+                     const gbf_options *opt, void *cuda_stream) {
+  if (!h || !srcs || !dist) return set_error("graph, srcs or dist is NULL"), GBF_ERR_INVALID;
+  Graph &g = h->g;
+  if (k < 1 || k > 64) return set_error("k must be in [1, 64]"), GBF_ERR_INVALID;
+  for (int i = 0; i < k; i++)
+    if (srcs[i] < 0 || srcs[i] >= g.n) return set_error("source out of range"), GBF_ERR_INVALID;
+  if (mem != GBF_HOST && mem != GBF_DEVICE) return set_error("bad mem"), GBF_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  std::lock_guard<std::mutex> lk(g.mu);
+  GBF_TRY(ws_ensure_msbfs(g, g.ws, mem == GBF_HOST));
+  const Opts o = resolve(opt, g);
+  int32_t *dd = mem == GBF_HOST ? g.ws.ms_dist_tmp : dist;
+  GBF_TRY(launch_msbfs(g, g.ws, srcs, k, dd, o, st));
+  if (mem == GBF_DEVICE) return GBF_OK;
+  GBF_CUDA(cudaMemcpyAsync(dist, dd, sizeof(int32_t) * (size_t)k * (size_t)g.n,
+                           cudaMemcpyDeviceToHost, st));
+  return ws_collect(g.ws, st, nullptr);
 }
 
 gbf_status gbf_wait(gbf_graph *h, void *cuda_stream, gbf_stats *stats) {

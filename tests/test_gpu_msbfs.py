@@ -1,0 +1,94 @@
+"""GPU parity for the 64-lane multi-source BFS: lane i must equal a BFS from
+srcs[i] (the oracle's, bit-exact), for every lane, on seeded graphs, with
+duplicate and isolated sources, both directions of edgeMap, and CUDA-graph
+replays with new sources and new output buffers."""
+import numpy as np
+import pytest
+
+import graphgen as G
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gb():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1805_05208_gb300 as gb
+    return gb
+
+
+def _check(gb, csr, srcs, opts=(None,)):
+    g = gb.Graph(csr)
+    ref = oracle.msbfs(csr, srcs)
+    for o in opts:
+        d = g.msbfs(srcs, opt=o)
+        assert d.shape == (len(srcs), csr.n)
+        bad = np.flatnonzero((d != ref).any(axis=1))
+        assert bad.size == 0, (csr.name, o and o.pull_divisor, bad[:5])
+    g.close()
+
+
+@pytest.mark.parametrize("scale,ef", [(10, 8), (14, 16), (16, 16)])
+def test_msbfs_rmat_64_lanes(gb, scale, ef):
+    csr = G.rmat(scale, ef, seed=30 + scale)
+    srcs = G.sources(csr, 64, seed=4)
+    _check(gb, csr, srcs, opts=(None, gb.gbf_options_default(pull_divisor=-1),
+                                gb.gbf_options_default(pull_divisor=1000),
+                                gb.gbf_options_default(block=512, heavy_cutoff=1024, ctas=5)))
+
+
+def test_msbfs_k_sizes_duplicates_isolated(gb):
+    csr = G.rmat(12, 8, seed=7)
+    deg = csr.degrees()
+    iso = np.flatnonzero(deg == 0)
+    s = list(G.sources(csr, 40, seed=9))
+    s[3] = s[7]                      # duplicate lane
+    if iso.size:
+        s[5] = int(iso[0])           # an isolated source
+    for k in (1, 2, 31, 32, 33, 40):
+        _check(gb, csr, np.array(s[:k], dtype=np.int32))
+
+
+def test_msbfs_grid_and_paths(gb):
+    _check(gb, G.grid(60, 70, 0.1, seed=3), np.array([0, 100, 4199, 2000], dtype=np.int32))
+    _check(gb, G.path_graph(300), np.arange(0, 300, 5, dtype=np.int32)[:60])
+    comp = G.csr_from_edges(20, [(0, 1), (1, 2), (5, 6), (6, 7), (10, 11)])
+    _check(gb, comp, np.arange(20, dtype=np.int32))
+
+
+def test_msbfs_graph_replay_new_sources_and_buffers(gb):
+    import torch
+    csr = G.rmat(13, 16, seed=11)
+    g = gb.Graph(csr)
+    dev = torch.device("cuda")
+    for rep in range(3):
+        srcs = G.sources(csr, 64, seed=100 + rep)
+        out = torch.full((64, csr.n), -5, dtype=torch.int32, device=dev)
+        gb.gbf_msbfs(g.h, srcs, out)
+        st = gb.gbf_wait(g.h)
+        assert st["device_error"] == 0 and st["rounds"] >= 1
+        assert np.array_equal(out.cpu().numpy(), oracle.msbfs(csr, srcs))
+    g.close()
+
+
+def test_msbfs_matches_single_bfs(gb):
+    csr = G.rmat(14, 8, seed=21)
+    g = gb.Graph(csr)
+    srcs = G.sources(csr, 64, seed=22)
+    d = g.msbfs(srcs)
+    for i in (0, 17, 63):
+        single, _ = g.bfs(int(srcs[i]))
+        assert np.array_equal(d[i], single)
+
+
+def test_msbfs_invalid(gb):
+    csr = G.path_graph(10)
+    g = gb.Graph(csr)
+    out = np.empty((65, 10), dtype=np.int32)
+    with pytest.raises(gb.GbfError):
+        gb.gbf_msbfs(g.h, np.zeros(65, dtype=np.int32), out)
+    with pytest.raises(gb.GbfError):
+        gb.gbf_msbfs(g.h, np.array([10], dtype=np.int32), out[:1])
