@@ -49,6 +49,11 @@ WORKLOADS = {
                        desc="BFS (dist+parent), RMAT scale 26 ef16 (~2.1B arcs), 4 seeded sources"),
     "wbfs-rmat26": dict(kind="wbfs", graph="rmat", scale=26, ef=16, w=(1, 22), nsrc=2,
                         desc="wBFS, RMAT scale 26 ef16, w in [1,22), 2 seeded sources"),
+    "msbfs-rmat24": dict(kind="msbfs", graph="rmat", scale=24, ef=16, w=None, nsrc=64,
+                         desc="multi-source BFS, 64 seeded sources in one uint64-lane launch, "
+                              "RMAT scale 24 ef16, autotuned; vs 64 single-source BFS launches"),
+    "msbfs-rmat20": dict(kind="msbfs", graph="rmat", scale=20, ef=16, w=None, nsrc=64,
+                         desc="multi-source BFS, 64 sources, RMAT scale 20 (profiling size)"),
     "bfs-grid": dict(kind="bfs", graph="grid", R=4096, C=4096, w=None, nsrc=4,
                      desc="BFS, 4096x4096 grid, 10% edges deleted, source 0 + 3 seeded"),
     "wbfs-grid": dict(kind="wbfs", graph="grid", R=4096, C=4096, w=(1, 16), nsrc=4,
@@ -156,6 +161,12 @@ def bytes_model(kind, n, st):
         # and the bucket write (8); per heavy vertex: queue + degree prefix
         # written and read (16)
         return 4 * n + 16 * I + 12 * E + 8 * R + 16 * st["heavy_vertices"]
+    if kind == "msbfs":
+        # init seen/visit/next (32n); every dist[i][v] written once (4kn); per
+        # scanned arc: target + the neighbour's lane word (12); per frontier
+        # vertex / pull candidate: offsets, lane words, queue (24); per dense
+        # level: seen read and next-lane word written for every vertex (16n)
+        return 32 * n + 4 * 64 * n + 12 * E + 24 * V + 16 * n * st["pull_rounds"]
     # BFS: init D, parent (8n) + visited bitmap (n/8); per frontier vertex or
     # pull candidate: queue/offset reads (12); per arc: target + bitmap word (8);
     # per reached vertex: D, parent, offsets, queue+qoff write (24); bitmaps per
@@ -228,6 +239,128 @@ def run_reference(args, wl, rank, world):
     return 0
 
 
+def run_msbfs(args, wl, g, srcs, graph, opt, stream, dev, rank, world, barrier, dist_mod):
+    """One step = one multi-source BFS launch over the 64 sources; the same
+    64 sources as single-source launches are timed beside it."""
+    import torch
+    import paper_1805_05208_gb300 as gb
+    n, k = g.n, len(srcs)
+    if not args.opt:
+        opt = gb.gbf_autotune(graph.h, gb.TUNE_MSBFS)
+    tuned = {f: getattr(opt, f) for f in ("block", "pull_divisor", "heavy_cutoff")}
+    out = torch.empty((k, n), dtype=torch.int32, device=dev)
+    deg = torch.from_numpy(np.diff(g.off.astype(np.int64))).to(dev)
+    stats = None
+    for w in range(args.warmup):
+        gb.gbf_msbfs(graph.h, srcs, out, opt, stream)
+        if w == 0:
+            stats = gb.gbf_wait(graph.h, stream)
+            trace0 = gb.gbf_trace(graph.h)
+    gb.gbf_wait(graph.h, stream)
+    te_step = int(((out != INF).to(torch.int64) * deg).sum().item() // 2)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for s_ in range(args.steps):
+            ev[s_][0].record(stream)
+            gb.gbf_msbfs(graph.h, srcs, out, opt, stream)
+            ev[s_][1].record(stream)
+        t1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    st = gb.gbf_wait(graph.h, stream)
+    if st["device_error"]:
+        raise RuntimeError(f"device error {st['device_error']}")
+    ms_total = t0.elapsed_time(t1)
+    # the comparison: the same 64 queries as one single-source launch each
+    d1 = torch.empty(n, dtype=torch.int32, device=dev)
+    bopt = gb.gbf_autotune(graph.h, gb.TUNE_BFS) if not args.opt else opt
+    for s_ in srcs[:4]:
+        gb.gbf_bfs(graph.h, int(s_), d1, None, bopt, stream)
+    gb.gbf_wait(graph.h, stream)
+    torch.cuda.synchronize()
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for s_ in srcs:
+        gb.gbf_bfs(graph.h, int(s_), d1, None, bopt, stream)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    ms_single64 = a0.elapsed_time(a1)
+    if world > 1:
+        t = torch.tensor([ms_total], device=dev)
+        dist_mod.all_reduce(t, op=dist_mod.ReduceOp.MAX)
+        ms_total = float(t.item())
+        tt = torch.tensor([float(te_step)], device=dev, dtype=torch.float64)
+        dist_mod.all_reduce(tt)
+        te_all = float(tt.item())
+    else:
+        te_all = float(te_step)
+    value = te_all * args.steps / (ms_total / 1e3) / 1e9
+    launch_ms = [e[0].elapsed_time(e[1]) for e in ev]
+    peak, peak_kind = load_peaks()
+    bpl = bytes_model("msbfs", n, stats)
+    avg = sum(launch_ms) / len(launch_ms)
+    # end to end: host output buffer, the 64 x n result copied back each step
+    host = torch.empty((k, n), dtype=torch.int32, pin_memory=True).numpy()
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    barrier()
+    tt0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        gb.gbf_msbfs(graph.h, srcs, host, opt, None)
+    e2e_s = time.perf_counter() - tt0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist_mod.all_reduce(t, op=dist_mod.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            te_c, t_c, q = cpu_reference_sample(g, dict(wl, kind="bfs"), srcs,
+                                                budget_s=args.cpu_budget)
+            cpu = {"value": te_c / t_c / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                   "sample": f"{q} of the {k} single-source oracle BFS runs of one step, "
+                             f"{t_c:.1f} s"}
+        clocks = clk.summary()
+        line = {
+            "metric": "GTEPS", "value": value, "unit": "GTEPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "uint64-lanes/int32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "desc": wl["desc"], "n": n, "arcs": g.m,
+                       "sources_per_step": k, "seeds": {"graph": 1, "sources": 3},
+                       "l2": "inputs larger than L2; no flush", "tuned_options": tuned},
+            "vs_single_source_launches": {"ms_64_single": ms_single64,
+                                          "ms_one_msbfs": ms_total / args.steps,
+                                          "speedup": ms_single64 / (ms_total / args.steps),
+                                          "single_options": {f: getattr(bopt, f) for f in
+                                                             ("block", "pull_divisor", "heavy_cutoff")}},
+            "roofline": {"bound": "hbm", "kernel": "msbfs_kernel", "achieved": bpl / (avg / 1e3) / 1e9,
+                         "peak": peak, "unit": "GB/s", "frac": bpl / (avg / 1e3) / 1e9 / peak,
+                         "peak_source": f"{peak_kind} hbm_gbs (burst copy)", "bytes_per_launch": bpl,
+                         "avg_launch_ms": avg, "traffic": None},
+            "cpu_baseline": cpu,
+            "e2e": {"value": te_all * e2e_steps / e2e_s / 1e9, "unit": "GTEPS",
+                    "h2d_bytes_per_step": 4 * k, "d2h_bytes_per_step": 4 * k * n},
+            "gpu_launches": args.steps,
+            "clocks": {kk: clocks[kk] for kk in ("sm_mhz", "sm_max_mhz", "reasons")},
+            "stats": {"levels": stats["rounds"], "pull_levels": stats["pull_rounds"],
+                      "edges_scanned": stats["edges_scanned"], "traversed_edges_per_step": te_step,
+                      "grid_ctas": stats["grid_ctas"], "block": stats["block"],
+                      "query0_trace": trace_summary(trace0)},
+        }
+        print(json.dumps(line))
+    graph.close()
+    if world > 1:
+        dist_mod.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -272,6 +405,8 @@ def main():
     graph = gb.Graph(g, validate=gb.VALIDATE_BASIC)
     stream = torch.cuda.Stream(device=dev)
     kind = wl["kind"]
+    if kind == "msbfs":
+        return run_msbfs(args, wl, g, srcs, graph, opt, stream, dev, rank, world, barrier, dist_mod)
     outs = [torch.empty(n, dtype=torch.int32, device=dev) for _ in srcs]
     pars = [torch.empty(n, dtype=torch.int32, device=dev) for _ in srcs] if kind == "bfs" else None
 

@@ -200,6 +200,24 @@ gbf_status gbf_wait(gbf_graph *g, void *cuda_stream, gbf_stats *stats);
 gbf_status gbf_msbfs(gbf_graph *g, const int32_t *srcs, int32_t k, int32_t *dist, int mem,
                      const gbf_options *opt, void *cuda_stream);
 
+#define GBF_TUNE_BFS 0   /* tune gbf_bfs */
+#define GBF_TUNE_MSBFS 1 /* tune gbf_msbfs (64 lanes) */
+#define GBF_TUNE_WBFS 2  /* tune gbf_wbfs */
+
+/*
+ * gbf_autotune — choose block size, pull divisor (the m / divisor switch of
+ * edgeMap, §3) and heavy cutoff (the block size of the blocked edgeMap,
+ * §6.2) for queries of `kind` on g, by timing real queries (median of
+ * repeats over seeded sources) in a coordinate descent over block in
+ * {128, 256, 512, 1024}, divisor in {10, 14, 20, 28, 40} and heavy cutoff in
+ * {256, ..., 4096}.  Writes the fastest setting to *out (other fields at
+ * their defaults).  Results are cached per (graph fingerprint, device, kind)
+ * in the process, and across processes in the file named by the environment
+ * variable GBF_TUNE_CACHE if set.  Distances never depend on the knobs.
+ * Uses g's default workspace; blocks until done.
+ */
+gbf_status gbf_autotune(gbf_graph *g, int32_t kind, gbf_options *out);
+
 /* One record per round of the last query (see gbf_trace). */
 typedef struct {
   int32_t round;          /* 1-based round (BFS level or wBFS bucket round) */

@@ -85,6 +85,7 @@ def _load() -> ctypes.CDLL:
         "gbf_wbfs": (S, [P, I32, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
         "gbf_wait": (S, [P, P, ctypes.POINTER(gbf_stats)]),
         "gbf_msbfs": (S, [P, P, I32, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
+        "gbf_autotune": (S, [P, I32, ctypes.POINTER(gbf_options)]),
         "gbf_trace": (S, [P, ctypes.POINTER(gbf_round_trace), I32, ctypes.POINTER(I32)]),
         "gbf_bfs_noalloc": (S, [I32, U32, P, P, I32, P, P, ctypes.POINTER(gbf_options), P]),
     }
@@ -203,6 +204,16 @@ def gbf_msbfs(h: int, srcs, dist, opt: Optional[gbf_options] = None, stream=None
     pd, mem = _ptr(dist)
     _check(_lib.gbf_msbfs(h, s.ctypes.data, int(s.size), pd, mem, _opt(opt), _stream(stream)),
            "gbf_msbfs")
+
+
+TUNE_BFS, TUNE_MSBFS, TUNE_WBFS = 0, 1, 2
+
+
+def gbf_autotune(h: int, kind: int = TUNE_BFS) -> gbf_options:
+    """Time the knob grid on this graph and return the fastest options."""
+    o = gbf_options()
+    _check(_lib.gbf_autotune(h, int(kind), ctypes.byref(o)), "gbf_autotune")
+    return o
 
 
 def gbf_wait(h: int, stream=None) -> dict:

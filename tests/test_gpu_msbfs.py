@@ -92,3 +92,29 @@ def test_msbfs_invalid(gb):
         gb.gbf_msbfs(g.h, np.zeros(65, dtype=np.int32), out)
     with pytest.raises(gb.GbfError):
         gb.gbf_msbfs(g.h, np.array([10], dtype=np.int32), out[:1])
+
+
+def test_autotune_results_invariant(gb, tmp_path, monkeypatch):
+    """The tuner returns valid knobs, caches them, and the tuned queries give
+    the same distances (knobs never change results)."""
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("GBF_TUNE_CACHE", str(cache))
+    csr = G.add_weights(G.rmat(13, 16, seed=41), 1, 22, seed=42)
+    g = gb.Graph(csr)
+    srcs = G.sources(csr, 64, seed=43)
+    for kind in (gb.TUNE_BFS, gb.TUNE_MSBFS, gb.TUNE_WBFS):
+        o = gb.gbf_autotune(g.h, kind)
+        assert o.block in (128, 256, 512, 1024)
+        assert o.pull_divisor in (10, 14, 20, 28, 40)
+        assert o.heavy_cutoff in (256, 512, 1024, 2048, 4096)
+        o2 = gb.gbf_autotune(g.h, kind)          # cached
+        assert (o2.block, o2.pull_divisor, o2.heavy_cutoff) == (o.block, o.pull_divisor,
+                                                                o.heavy_cutoff)
+        s = int(srcs[0])
+        if kind == gb.TUNE_BFS:
+            assert np.array_equal(g.bfs(s, opt=o)[0], oracle.bfs(csr, s)[0])
+        elif kind == gb.TUNE_WBFS:
+            assert np.array_equal(g.wbfs(s, opt=o), oracle.dijkstra(csr, s))
+        else:
+            assert np.array_equal(g.msbfs(srcs, opt=o), oracle.msbfs(csr, srcs))
+    assert len(cache.read_text().splitlines()) == 3
