@@ -218,6 +218,81 @@ gbf_status gbf_msbfs(gbf_graph *g, const int32_t *srcs, int32_t k, int32_t *dist
  */
 gbf_status gbf_autotune(gbf_graph *g, int32_t kind, gbf_options *out);
 
+/* ------------------------------------------------------------------ serving
+ * A continuous-batching query server over several resident graphs.  BFS
+ * and weighted-BFS queries (§4 problem statements) are admitted while a
+ * device result slot is free (slots are carved once from an HBM budget) and
+ * the pending queue has room.  A dispatcher thread keeps engines busy, each
+ * with its own stream and workspace: BFS engines coalesce up to max_batch
+ * pending BFS queries of one graph into one 64-lane multi-source launch
+ * (each lane writes its query's result slot); wBFS engines run one weighted
+ * query each.  Engines run concurrently on equal shares of the GPU.
+ * Results stay on the device until polled.  The paper has no serving layer;
+ * results are identical to the single-query calls.
+ */
+typedef struct gbf_server gbf_server;
+
+#define GBF_QUERY_BFS 0
+#define GBF_QUERY_WBFS 1
+
+typedef struct {
+  int32_t bfs_engines;   /* concurrent BFS batches (default 2) */
+  int32_t wbfs_engines;  /* concurrent weighted queries (default 2; unused without weighted graphs) */
+  int32_t max_batch;     /* BFS queries per launch, 1..64 (default 64); 1 = one query per launch
+                            with the single-source BFS kernel */
+  int32_t max_queue;     /* pending queries before submit returns GBF_ERR_BUSY (default 65536) */
+  size_t hbm_budget;     /* device bytes for result slots (0 = a quarter of free HBM) */
+  gbf_options kernel;    /* kernel knobs (ctas is capped to the engine's share) */
+} gbf_server_options;
+
+typedef struct {
+  uint64_t completed;       /* queries finished successfully */
+  uint64_t failed;          /* queries finished with a device or launch error */
+  uint64_t pending;         /* admitted, not finished */
+  uint64_t batches;         /* BFS launches */
+  uint64_t batched_queries; /* BFS queries carried by those launches */
+  uint64_t free_slots;      /* result slots available for admission */
+  int32_t engines;
+  int32_t reserved;
+} gbf_server_counters;
+
+/* Fills *opt with the defaults. */
+gbf_status gbf_server_options_default(gbf_server_options *opt);
+
+/* Start a server over ngraphs resident graphs (handles stay owned by the
+ * caller and must outlive the server).  Reserves the result slots and the
+ * engines' workspaces up front; GBF_ERR_OOM if they do not fit. */
+gbf_status gbf_server_create(gbf_graph *const *graphs, int32_t ngraphs,
+                             const gbf_server_options *opt, gbf_server **out);
+
+/* Admit a query (kind GBF_QUERY_BFS or GBF_QUERY_WBFS) from src on graph
+ * graph_idx; *ticket identifies it.  GBF_ERR_BUSY if no result slot is free
+ * or the queue is full (try again later); GBF_ERR_INVALID for bad
+ * arguments.  Thread-safe. */
+gbf_status gbf_server_submit(gbf_server *s, int32_t graph_idx, int32_t kind, int32_t src,
+                             uint64_t *ticket);
+
+/* Poll a ticket: *done = 0 while it runs.  Once done, copies its distances
+ * (n int32, GBF_INF if unreachable) to dist_host if non-NULL, stores the
+ * submit-to-completion latency in *latency_us (if non-NULL), releases the
+ * ticket and its slot, and returns the query's status.  GBF_ERR_NOT_FOUND
+ * for an unknown or already released ticket.  Thread-safe. */
+gbf_status gbf_server_poll(gbf_server *s, uint64_t ticket, int32_t *dist_host, int32_t *done,
+                           double *latency_us);
+
+/* Release up to cap finished queries without copying their results (for
+ * callers that only need completion and latency): their tickets, latencies
+ * (if non-NULL) and statuses (if non-NULL) go to the arrays, their number
+ * to *count.  Thread-safe. */
+gbf_status gbf_server_collect(gbf_server *s, uint64_t *tickets, double *latency_us,
+                              int32_t *status, int32_t cap, int32_t *count);
+
+/* Counters since creation. */
+gbf_status gbf_server_stats(gbf_server *s, gbf_server_counters *out);
+
+/* Stop the dispatcher (running launches finish first) and free everything. */
+gbf_status gbf_server_destroy(gbf_server *s);
+
 /* One record per round of the last query (see gbf_trace). */
 typedef struct {
   int32_t round;          /* 1-based round (BFS level or wBFS bucket round) */

@@ -59,6 +59,22 @@ class gbf_stats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
 
 
+class gbf_server_options(ctypes.Structure):
+    _fields_ = [("bfs_engines", ctypes.c_int32), ("wbfs_engines", ctypes.c_int32),
+                ("max_batch", ctypes.c_int32), ("max_queue", ctypes.c_int32),
+                ("hbm_budget", ctypes.c_size_t), ("kernel", gbf_options)]
+
+
+class gbf_server_counters(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
+                ("pending", ctypes.c_uint64), ("batches", ctypes.c_uint64),
+                ("batched_queries", ctypes.c_uint64), ("free_slots", ctypes.c_uint64),
+                ("engines", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
 class gbf_round_trace(ctypes.Structure):
     _fields_ = [("round", ctypes.c_int32), ("kind", ctypes.c_int32), ("frontier", ctypes.c_uint32),
                 ("frontier_edges", ctypes.c_uint32), ("t_ns", ctypes.c_int64),
@@ -85,6 +101,13 @@ def _load() -> ctypes.CDLL:
         "gbf_wbfs": (S, [P, I32, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
         "gbf_wait": (S, [P, P, ctypes.POINTER(gbf_stats)]),
         "gbf_msbfs": (S, [P, P, I32, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
+        "gbf_server_options_default": (S, [ctypes.POINTER(gbf_server_options)]),
+        "gbf_server_create": (S, [P, I32, ctypes.POINTER(gbf_server_options), ctypes.POINTER(P)]),
+        "gbf_server_submit": (S, [P, I32, I32, I32, ctypes.POINTER(U64)]),
+        "gbf_server_poll": (S, [P, U64, P, ctypes.POINTER(I32), ctypes.POINTER(ctypes.c_double)]),
+        "gbf_server_collect": (S, [P, P, P, P, I32, ctypes.POINTER(I32)]),
+        "gbf_server_stats": (S, [P, ctypes.POINTER(gbf_server_counters)]),
+        "gbf_server_destroy": (S, [P]),
         "gbf_autotune": (S, [P, I32, ctypes.POINTER(gbf_options)]),
         "gbf_trace": (S, [P, ctypes.POINTER(gbf_round_trace), I32, ctypes.POINTER(I32)]),
         "gbf_bfs_noalloc": (S, [I32, U32, P, P, I32, P, P, ctypes.POINTER(gbf_options), P]),
@@ -244,6 +267,67 @@ def gbf_bfs_noalloc(n: int, m: int, off, tgt, src: int, dist, parent=None,
             raise ValueError("gbf_bfs_noalloc takes device buffers only")
     _check(_lib.gbf_bfs_noalloc(int(n), int(m), po, pt, int(src), pd, pp, _opt(opt),
                                 _stream(stream)), "gbf_bfs_noalloc")
+
+
+QUERY_BFS, QUERY_WBFS = 0, 1
+
+
+def gbf_server_options_default(**overrides) -> gbf_server_options:
+    o = gbf_server_options()
+    _check(_lib.gbf_server_options_default(ctypes.byref(o)), "gbf_server_options_default")
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def gbf_server_create(graphs: Sequence[int], opt: Optional[gbf_server_options] = None) -> int:
+    arr = (ctypes.c_void_p * len(graphs))(*graphs)
+    h = ctypes.c_void_p()
+    _check(_lib.gbf_server_create(arr, len(graphs), None if opt is None else ctypes.byref(opt),
+                                  ctypes.byref(h)), "gbf_server_create")
+    return h.value
+
+
+def gbf_server_submit(s: int, graph_idx: int, kind: int, src: int):
+    """Returns the ticket, or None if the server is busy (GBF_ERR_BUSY)."""
+    t = ctypes.c_uint64()
+    st = _lib.gbf_server_submit(s, int(graph_idx), int(kind), int(src), ctypes.byref(t))
+    if st == 6:
+        return None
+    _check(st, "gbf_server_submit")
+    return t.value
+
+
+def gbf_server_poll(s: int, ticket: int, dist=None):
+    """Returns (done, latency_us); fills dist (numpy int32[n]) when done."""
+    done = ctypes.c_int32()
+    lat = ctypes.c_double()
+    pd = None if dist is None else _ptr(dist)[0]
+    _check(_lib.gbf_server_poll(s, ctypes.c_uint64(ticket), pd, ctypes.byref(done),
+                                ctypes.byref(lat)), "gbf_server_poll")
+    return bool(done.value), lat.value
+
+
+def gbf_server_collect(s: int, cap: int = 65536):
+    """Release finished queries without copying results: (tickets, latency_us, status)."""
+    t = np.empty(cap, dtype=np.uint64)
+    lat = np.empty(cap, dtype=np.float64)
+    stt = np.empty(cap, dtype=np.int32)
+    cnt = ctypes.c_int32()
+    _check(_lib.gbf_server_collect(s, t.ctypes.data, lat.ctypes.data, stt.ctypes.data, cap,
+                                   ctypes.byref(cnt)), "gbf_server_collect")
+    k = cnt.value
+    return t[:k], lat[:k], stt[:k]
+
+
+def gbf_server_stats(s: int) -> dict:
+    o = gbf_server_counters()
+    _check(_lib.gbf_server_stats(s, ctypes.byref(o)), "gbf_server_stats")
+    return o.as_dict()
+
+
+def gbf_server_destroy(s: int) -> None:
+    _check(_lib.gbf_server_destroy(s), "gbf_server_destroy")
 
 
 class Graph:

@@ -146,6 +146,8 @@ gbf_status launch_wbfs(Graph &g, Workspace &ws, int32_t src, int32_t *dist, cons
                        cudaStream_t st);
 gbf_status launch_msbfs(Graph &g, Workspace &ws, const int32_t *srcs_host, int32_t k,
                         int32_t *dist, const Opts &o, cudaStream_t st);
+gbf_status launch_msbfs_rows(Graph &g, Workspace &ws, const int32_t *srcs_host, int32_t k,
+                             int32_t *const *rows, const Opts &o, cudaStream_t st);
 
 }  // namespace gbf
 

@@ -237,14 +237,14 @@ gbf_status ws_ensure_msbfs(Graph &g, Workspace &ws, bool host_out) {
     GBF_TRY(dmalloc(&ws.ms_cs[2], cs, acc));
     GBF_TRY(dmalloc(&ws.ms_touched, n, acc));
     char *call = nullptr;
-    GBF_TRY(dmalloc(&call, 512, acc));
+    GBF_TRY(dmalloc(&call, 1024, acc));
     ws.ms_call = call;
     for (int i = 0; i < 2; i++) {
       ws.ms_q[i] = ws.q[i];
       ws.ms_qoff[i] = ws.qoff[i];
       ws.ms_cs[i] = ws.cs[i];
     }
-    GBF_CUDA(cudaMallocHost(&ws.ms_call_host, 512));
+    GBF_CUDA(cudaMallocHost(&ws.ms_call_host, 1024));
     GBF_CUDA(cudaStreamCreateWithFlags(&ws.ms_stream, cudaStreamNonBlocking));
     GBF_CUDA(cudaEventCreateWithFlags(&ws.ms_ready, cudaEventDisableTiming));
     GBF_CUDA(cudaEventCreateWithFlags(&ws.ms_done, cudaEventDisableTiming));

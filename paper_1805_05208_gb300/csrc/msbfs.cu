@@ -19,8 +19,9 @@
 // warp-wide bit loops so a warp of consecutive vertices writes each row
 // coalesced; lanes that never reach a vertex get GBF_INF at the end.
 //
-// Sources, k and the output pointer are read from a device parameter block
-// (MsCall), so one captured CUDA graph replays any call.
+// The graph, sources, k and the output rows are read from a device parameter
+// block (MsCall), so one captured CUDA graph replays any call on any graph
+// the workspace is sized for.
 #include <cuda_runtime.h>
 
 #include "dev_common.cuh"
@@ -30,14 +31,14 @@ namespace gbf {
 using namespace dev;
 
 struct MsCall {
+  DevGraph g;         // the graph of this call
   int32_t srcs[64];
+  int32_t *rows[64];  // rows[i][v] = distance of v from srcs[i]
   int32_t k;
   int32_t pad;
-  int32_t *dist;
 };
 
 struct MsParams {
-  DevGraph g;
   const MsCall *call;
   unsigned long long *seen;
   unsigned long long *visit[2];
@@ -65,7 +66,7 @@ typedef unsigned long long u64;
 // Warp-collective: write level L into dist[i][v] for every lane bit i of
 // `bits`, iterating lanes so that a warp of consecutive v writes each row
 // with one coalesced store.
-__device__ __forceinline__ void write_rows(int32_t *dist, uint32_t n, int k, int32_t v, u64 bits,
+__device__ __forceinline__ void write_rows(int32_t *const *rows, int k, int32_t v, u64 bits,
                                            int32_t L) {
   u64 any = 0;
   // OR of bits across the warp, to skip lanes nobody has
@@ -76,7 +77,7 @@ __device__ __forceinline__ void write_rows(int32_t *dist, uint32_t n, int k, int
     const int i = __ffsll((long long)any) - 1;
     any &= any - 1;
     if (i >= k) break;
-    if ((bits >> i) & 1ull) dist[(size_t)i * n + (uint32_t)v] = L;
+    if ((bits >> i) & 1ull) rows[i][v] = L;
   }
 }
 
@@ -142,12 +143,12 @@ __global__ void __launch_bounds__(1024) msbfs_kernel(MsParams P) {
   if (threadIdx.x == 0) S.misc[0] = 0;
   Ctl *ctl = P.ctl;
   Barrier bar{0u, P.cap_ns};
-  const DevGraph g = P.g;
+  const DevGraph g = P.call->g;
   const uint32_t n = (uint32_t)g.n;
   const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int k = P.call->k;
-  int32_t *dist = P.call->dist;
+  int32_t *const *rows = P.call->rows;
   const u64 ALL = (k >= 64) ? ~0ull : ((1ull << k) - 1ull);
   unsigned long long scanned = 0, expanded = 0, reached = 0;
   const unsigned long long t_start = globaltimer();
@@ -170,7 +171,7 @@ __global__ void __launch_bounds__(1024) msbfs_kernel(MsParams P) {
       s = P.call->srcs[threadIdx.x];
       atomicOr(P.seen + s, 1ull << threadIdx.x);
       atomicOr(P.visit[0] + s, 1ull << threadIdx.x);
-      dist[(size_t)threadIdx.x * n + (uint32_t)s] = 0;
+      rows[threadIdx.x][s] = 0;
       bool dup = false;
       for (int j = 0; j < (int)threadIdx.x; j++) dup |= P.call->srcs[j] == s;
       d = __ldg(g.off + s + 1) - __ldg(g.off + s);
@@ -243,7 +244,7 @@ __global__ void __launch_bounds__(1024) msbfs_kernel(MsParams P) {
         while (bits) {
           const int bi = __ffsll((long long)bits) - 1;
           bits &= bits - 1;
-          if (bi < k) dist[(size_t)bi * n + (uint32_t)v] = L;
+          if (bi < k) rows[bi][v] = L;
         }
         stage_append(S, nwb != 0ull && d > 0, v, d);
         __syncthreads();
@@ -306,7 +307,7 @@ __global__ void __launch_bounds__(1024) msbfs_kernel(MsParams P) {
           }
         }
         if (cand) expanded++;
-        write_rows(dist, n, k, v, inr ? nwb : 0ull, L);
+        write_rows(rows, k, v, inr ? nwb : 0ull, L);
         stage_append(S, nwb != 0ull && e > s, v, e - s);
         __syncthreads();
         if (S.misc[0] + blockDim.x > S.cap_out) stage_flush(S, fout, ctl);
@@ -325,7 +326,7 @@ __global__ void __launch_bounds__(1024) msbfs_kernel(MsParams P) {
     for (uint32_t wi = gw; wi < nwords; wi += tw) {
       const uint32_t v = wi * 32 + lane;
       const u64 miss = (v < n) ? (ALL & ~P.seen[v]) : 0ull;
-      write_rows(dist, n, k, (int32_t)v, miss, kInf);
+      write_rows(rows, k, (int32_t)v, miss, kInf);
     }
   }
   unsigned long long tt;
@@ -339,15 +340,19 @@ __global__ void __launch_bounds__(1024) msbfs_kernel(MsParams P) {
 
 // Host side: a CUDA graph per workspace holding [parameter copy, control
 // reset, cooperative kernel], replayed for every call with the same knobs.
-gbf_status launch_msbfs(Graph &g, Workspace &ws, const int32_t *srcs_host, int32_t k,
-                        int32_t *dist, const Opts &o, cudaStream_t user_st) {
+gbf_status launch_msbfs_rows(Graph &g, Workspace &ws, const int32_t *srcs_host, int32_t k,
+                             int32_t *const *rows, const Opts &o, cudaStream_t user_st) {
+  static_assert(sizeof(MsCall) <= 1024, "parameter block size");
   // the previous replay must be done with the pinned parameter block
   if (ws.ms_done) GBF_CUDA(cudaEventSynchronize(ws.ms_done));
   MsCall *hc = (MsCall *)ws.ms_call_host;
-  for (int i = 0; i < 64; i++) hc->srcs[i] = i < k ? srcs_host[i] : 0;
+  hc->g = g.dev();
+  for (int i = 0; i < 64; i++) {
+    hc->srcs[i] = i < k ? srcs_host[i] : 0;
+    hc->rows[i] = i < k ? rows[i] : nullptr;
+  }
   hc->k = k;
   hc->pad = 0;
-  hc->dist = dist;
   const long long key[6] = {o.block, o.pull_divisor, o.heavy_cutoff, o.pull_serial, o.ctas,
                             o.spin_cap_ns};
   bool same = ws.ms_exec != nullptr;
@@ -359,18 +364,17 @@ gbf_status launch_msbfs(Graph &g, Workspace &ws, const int32_t *srcs_host, int32
       ws.ms_exec = nullptr;
     }
     MsParams P;
-    P.g = g.dev();
     P.call = (const MsCall *)ws.ms_call;
     P.seen = ws.ms_seen;
     P.visit[0] = ws.ms_visit;
-    P.visit[1] = ws.ms_visit + (size_t)g.n;
+    P.visit[1] = ws.ms_visit + (size_t)ws.n;  // the workspace's size, not this graph's
     P.next = ws.ms_next;
     for (int i = 0; i < 3; i++) {
       P.q[i] = ws.ms_q[i];
       P.qoff[i] = ws.ms_qoff[i];
       P.cs[i] = ws.ms_cs[i];
     }
-    P.cs_cap = (uint32_t)(((uint64_t)g.m + kFine - 1) / kFine + 2);
+    P.cs_cap = (uint32_t)(((uint64_t)ws.m + kFine - 1) / kFine + 2);
     P.touched = ws.ms_touched;
     P.ctl = ws.ctl;
     P.trace = ws.trace;
@@ -426,6 +430,13 @@ gbf_status launch_msbfs(Graph &g, Workspace &ws, const int32_t *srcs_host, int32
   ws.last_grid = ws.ms_grid;
   ws.last_block = o.block;
   return GBF_OK;
+}
+
+gbf_status launch_msbfs(Graph &g, Workspace &ws, const int32_t *srcs_host, int32_t k,
+                        int32_t *dist, const Opts &o, cudaStream_t st) {
+  int32_t *rows[64];
+  for (int i = 0; i < 64; i++) rows[i] = i < k ? dist + (size_t)i * (size_t)g.n : nullptr;
+  return launch_msbfs_rows(g, ws, srcs_host, k, rows, o, st);
 }
 
 }  // namespace gbf

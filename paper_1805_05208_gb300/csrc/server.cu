@@ -1,0 +1,450 @@
+// Continuous-batching query server over several resident graphs.
+//
+// Requests (BFS or weighted BFS from one source on one graph) are admitted
+// while a result slot of device memory is free (the slots are carved once
+// from an HBM budget) and the pending queue has room; otherwise submit
+// returns GBF_ERR_BUSY.  A dispatcher thread keeps a set of engines busy,
+// each with its own CUDA stream and workspace:
+//   - BFS engines take up to max_batch pending BFS requests of one graph
+//     (the graph whose oldest request is oldest) and run them as one 64-lane
+//     multi-source BFS launch whose lane i writes straight into request i's
+//     result slot; with max_batch = 1 they run the single-source BFS kernel
+//     instead (one query per launch);
+//   - wBFS engines take the oldest weighted request.
+// Engines run concurrently; each persistent launch gets an equal share of
+// the GPU's resident CTAs, so all engines' CTAs can be co-resident at once.
+// Results stay in their device slots until polled (copied to the caller or
+// dropped), which frees the slot.  Latency is measured from submit to the
+// dispatcher observing the launch's completion event.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "gbf_impl.h"
+
+namespace gbf {
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+  uint64_t ticket;
+  int graph;
+  int kind;
+  int32_t src;
+  int slot;
+  Clock::time_point t_submit;
+  Clock::time_point t_done;
+  int state;  // 0 pending, 1 running, 2 done, 3 failed
+  gbf_status status;
+};
+
+struct Engine {
+  int kind;  // GBF_QUERY_BFS or GBF_QUERY_WBFS
+  Graph shape;  // sizing descriptor (max n, m, w) for the workspace
+  Workspace ws;
+  cudaStream_t st = nullptr;
+  cudaEvent_t done = nullptr;
+  bool busy = false;
+  int graph = -1;
+  std::vector<uint64_t> batch;
+};
+
+}  // namespace
+}  // namespace gbf
+
+struct gbf_server {
+  std::vector<gbf::Graph *> graphs;
+  gbf_server_options opt;
+  gbf::Opts kopt_bfs, kopt_wbfs;
+  int32_t max_n = 0;
+  char *slot_mem = nullptr;
+  size_t slot_bytes = 0;
+  std::vector<int> free_slots;
+  std::vector<gbf::Engine *> engines;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::unordered_map<uint64_t, gbf::Request> reqs;
+  std::vector<std::deque<uint64_t>> bfs_q;  // per graph
+  std::deque<uint64_t> wbfs_q;
+  uint64_t next_ticket = 1;
+  size_t pending = 0;
+  std::thread worker;
+  std::atomic<bool> stop{false};
+  // statistics
+  uint64_t completed = 0, failed = 0, batches = 0, batched_queries = 0;
+  int device = 0;
+};
+
+namespace gbf {
+namespace {
+
+int32_t *slot_ptr(gbf_server *s, int slot) {
+  return (int32_t *)(s->slot_mem + (size_t)slot * s->slot_bytes);
+}
+
+// Launch work on an idle engine; caller holds s->mu.
+void dispatch(gbf_server *s, Engine *e) {
+  if (e->kind == GBF_QUERY_WBFS) {
+    if (s->wbfs_q.empty()) return;
+    const uint64_t t = s->wbfs_q.front();
+    s->wbfs_q.pop_front();
+    Request &r = s->reqs[t];
+    Graph &g = *s->graphs[r.graph];
+    r.state = 1;
+    e->batch.assign(1, t);
+    e->graph = r.graph;
+    gbf_status st = launch_wbfs(g, e->ws, r.src, slot_ptr(s, r.slot), s->kopt_wbfs, e->st);
+    if (st != GBF_OK) {
+      r.state = 3;
+      r.status = st;
+      r.t_done = Clock::now();
+      s->failed++;
+      s->pending--;
+      return;
+    }
+    cudaEventRecord(e->done, e->st);
+    e->busy = true;
+    return;
+  }
+  // BFS engine: the graph whose oldest pending request is oldest
+  int best = -1;
+  Clock::time_point oldest = Clock::time_point::max();
+  for (size_t gi = 0; gi < s->bfs_q.size(); gi++) {
+    if (s->bfs_q[gi].empty()) continue;
+    const Request &r = s->reqs[s->bfs_q[gi].front()];
+    if (r.t_submit < oldest) {
+      oldest = r.t_submit;
+      best = (int)gi;
+    }
+  }
+  if (best < 0) return;
+  auto &q = s->bfs_q[best];
+  const int kmax = std::max(1, std::min(64, s->opt.max_batch));
+  e->batch.clear();
+  int32_t srcs[64];
+  int32_t *rows[64];
+  while (!q.empty() && (int)e->batch.size() < kmax) {
+    const uint64_t t = q.front();
+    q.pop_front();
+    Request &r = s->reqs[t];
+    r.state = 1;
+    srcs[e->batch.size()] = r.src;
+    rows[e->batch.size()] = slot_ptr(s, r.slot);
+    e->batch.push_back(t);
+  }
+  e->graph = best;
+  Graph &g = *s->graphs[best];
+  gbf_status st;
+  if (kmax == 1) st = launch_bfs(g, e->ws, srcs[0], rows[0], nullptr, s->kopt_bfs, e->st);
+  else st = launch_msbfs_rows(g, e->ws, srcs, (int32_t)e->batch.size(), rows, s->kopt_bfs, e->st);
+  if (st != GBF_OK) {
+    for (uint64_t t : e->batch) {
+      Request &r = s->reqs[t];
+      r.state = 3;
+      r.status = st;
+      r.t_done = Clock::now();
+      s->failed++;
+      s->pending--;
+    }
+    e->batch.clear();
+    return;
+  }
+  s->batches++;
+  s->batched_queries += e->batch.size();
+  cudaEventRecord(e->done, e->st);
+  e->busy = true;
+}
+
+void worker_loop(gbf_server *s) {
+  cudaSetDevice(s->device);
+  std::unique_lock<std::mutex> lk(s->mu);
+  while (!s->stop.load()) {
+    bool progress = false;
+    for (Engine *e : s->engines) {
+      if (!e->busy) continue;
+      const cudaError_t q = cudaEventQuery(e->done);
+      if (q == cudaErrorNotReady) continue;
+      const Clock::time_point now = Clock::now();
+      gbf_status st = GBF_OK;
+      if (q != cudaSuccess) {
+        cuda_fail(q, "engine completion");
+        st = GBF_ERR_CUDA;
+      } else {
+        gbf_stats sts;
+        st = ws_collect(e->ws, e->st, &sts);
+      }
+      for (uint64_t t : e->batch) {
+        auto it = s->reqs.find(t);
+        if (it == s->reqs.end()) continue;
+        it->second.state = st == GBF_OK ? 2 : 3;
+        it->second.status = st;
+        it->second.t_done = now;
+        if (st == GBF_OK) s->completed++;
+        else s->failed++;
+        s->pending--;
+      }
+      e->batch.clear();
+      e->busy = false;
+      progress = true;
+    }
+    for (Engine *e : s->engines) {
+      if (e->busy) continue;
+      dispatch(s, e);
+      if (e->busy) progress = true;
+    }
+    if (progress) s->cv.notify_all();
+    if (!progress) {
+      // idle: sleep until a submit arrives or a short poll interval passes
+      s->cv.wait_for(lk, std::chrono::microseconds(20));
+    }
+  }
+}
+
+void destroy_engine(Engine *e) {
+  if (e->st) cudaStreamSynchronize(e->st);
+  ws_free(e->ws);
+  if (e->done) cudaEventDestroy(e->done);
+  if (e->st) cudaStreamDestroy(e->st);
+  delete e;
+}
+
+}  // namespace
+}  // namespace gbf
+
+using namespace gbf;
+
+extern "C" {
+
+gbf_status gbf_server_options_default(gbf_server_options *o) {
+  if (!o) return GBF_ERR_INVALID;
+  memset(o, 0, sizeof(*o));
+  o->bfs_engines = 2;
+  o->wbfs_engines = 2;
+  o->max_batch = 64;
+  o->max_queue = 1 << 16;
+  o->hbm_budget = 0;
+  gbf_options_default(&o->kernel);
+  return GBF_OK;
+}
+
+gbf_status gbf_server_create(gbf_graph *const *graphs, int32_t ngraphs,
+                             const gbf_server_options *opt, gbf_server **out) {
+  if (!out || !graphs || ngraphs < 1) return set_error("bad arguments"), GBF_ERR_INVALID;
+  *out = nullptr;
+  gbf_server *s = new (std::nothrow) gbf_server();
+  if (!s) return set_error("host allocation failed"), GBF_ERR_OOM;
+  gbf_server_options_default(&s->opt);
+  if (opt) s->opt = *opt;
+  if (s->opt.bfs_engines < 0 || s->opt.wbfs_engines < 0 || s->opt.bfs_engines + s->opt.wbfs_engines < 1) {
+    delete s;
+    return set_error("need at least one engine"), GBF_ERR_INVALID;
+  }
+  s->opt.max_batch = std::max(1, std::min(64, s->opt.max_batch ? s->opt.max_batch : 64));
+  if (s->opt.max_queue <= 0) s->opt.max_queue = 1 << 16;
+  uint32_t max_m = 0, max_w = 0;
+  bool any_w = false;
+  for (int i = 0; i < ngraphs; i++) {
+    if (!graphs[i]) {
+      delete s;
+      return set_error("NULL graph"), GBF_ERR_INVALID;
+    }
+    Graph *g = &graphs[i]->g;
+    s->graphs.push_back(g);
+    s->max_n = std::max(s->max_n, g->n);
+    max_m = std::max(max_m, g->m);
+    if (g->w) {
+      any_w = true;
+      max_w = std::max(max_w, g->w_max);
+    }
+  }
+  s->device = s->graphs[0]->device;
+  s->bfs_q.resize(ngraphs);
+  auto fail = [&](gbf_status st) {
+    gbf_server_destroy(s);
+    return st;
+  };
+  // result slots from the HBM budget
+  s->slot_bytes = ((size_t)s->max_n * sizeof(int32_t) + 255) & ~(size_t)255;
+  size_t budget = s->opt.hbm_budget;
+  if (budget == 0) {
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    budget = fr / 4;
+  }
+  const size_t nslots = std::min<size_t>(budget / s->slot_bytes, 1 << 20);
+  if (nslots < 1) return fail((set_error("HBM budget below one result slot"), GBF_ERR_OOM));
+  cudaError_t e = cudaMalloc((void **)&s->slot_mem, nslots * s->slot_bytes);
+  if (e != cudaSuccess) return fail(cuda_fail(e, "result slots"));
+  s->free_slots.reserve(nslots);
+  for (size_t i = 0; i < nslots; i++) s->free_slots.push_back((int)(nslots - 1 - i));
+  // engines: an equal share of the resident CTAs each
+  const int nengines = s->opt.bfs_engines + (any_w ? s->opt.wbfs_engines : 0);
+  int sms = s->graphs[0]->num_sms;
+  for (int i = 0; i < nengines; i++) {
+    Engine *en = new (std::nothrow) Engine();
+    if (!en) return fail((set_error("host allocation failed"), GBF_ERR_OOM));
+    en->kind = i < s->opt.bfs_engines ? GBF_QUERY_BFS : GBF_QUERY_WBFS;
+    s->engines.push_back(en);
+    Graph &sh = en->shape;
+    sh.n = s->max_n;
+    sh.m = max_m;
+    sh.w_max = max_w;
+    sh.device = s->device;
+    sh.num_sms = sms;
+    if ((e = cudaStreamCreateWithFlags(&en->st, cudaStreamNonBlocking)) != cudaSuccess)
+      return fail(cuda_fail(e, "engine stream"));
+    if ((e = cudaEventCreateWithFlags(&en->done, cudaEventDisableTiming)) != cudaSuccess)
+      return fail(cuda_fail(e, "engine event"));
+    gbf_status st;
+    if (en->kind == GBF_QUERY_WBFS)
+      st = ws_ensure_wbfs(sh, en->ws, (int)std::min<uint32_t>(std::max<uint32_t>(max_w + 1, 2), 256));
+    else if (s->opt.max_batch > 1) st = ws_ensure_msbfs(sh, en->ws, false);
+    else st = ws_ensure_base(sh, en->ws);
+    if (st != GBF_OK) return fail(st);
+  }
+  // kernel knobs: an equal CTA share per engine (all engines co-resident)
+  gbf_options ko = s->opt.kernel;
+  s->kopt_bfs = resolve(&ko, *s->graphs[0]);
+  s->kopt_wbfs = s->kopt_bfs;
+  {
+    // resident CTAs per SM for the default block size is at least 1; a share
+    // of num_sms * 2 / engines keeps every engine resident even at 2 CTAs/SM
+    const int share = std::max(1, (sms * 2) / nengines);
+    if (s->kopt_bfs.ctas == 0 || s->kopt_bfs.ctas > share) s->kopt_bfs.ctas = share;
+    if (s->kopt_wbfs.ctas == 0 || s->kopt_wbfs.ctas > share) s->kopt_wbfs.ctas = share;
+  }
+  s->worker = std::thread(worker_loop, s);
+  *out = s;
+  return GBF_OK;
+}
+
+gbf_status gbf_server_submit(gbf_server *s, int32_t graph_idx, int32_t kind, int32_t src,
+                             uint64_t *ticket) {
+  if (!s || !ticket) return set_error("NULL argument"), GBF_ERR_INVALID;
+  if (graph_idx < 0 || graph_idx >= (int32_t)s->graphs.size())
+    return set_error("graph index out of range"), GBF_ERR_INVALID;
+  if (kind != GBF_QUERY_BFS && kind != GBF_QUERY_WBFS) return set_error("bad kind"), GBF_ERR_INVALID;
+  Graph &g = *s->graphs[graph_idx];
+  if (src < 0 || src >= g.n) return set_error("src out of range"), GBF_ERR_INVALID;
+  if (kind == GBF_QUERY_WBFS && !g.w) return set_error("graph has no weights"), GBF_ERR_INVALID;
+  bool has_engine = false;
+  for (Engine *e : s->engines) has_engine |= e->kind == kind;
+  if (!has_engine) return set_error("no engine for this kind"), GBF_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->free_slots.empty() || s->pending >= (size_t)s->opt.max_queue) {
+    set_error("server busy: no free result slot or queue full");
+    return GBF_ERR_BUSY;
+  }
+  Request r;
+  r.ticket = s->next_ticket++;
+  r.graph = graph_idx;
+  r.kind = kind;
+  r.src = src;
+  r.slot = s->free_slots.back();
+  s->free_slots.pop_back();
+  r.t_submit = Clock::now();
+  r.state = 0;
+  r.status = GBF_OK;
+  s->reqs.emplace(r.ticket, r);
+  if (kind == GBF_QUERY_BFS) s->bfs_q[graph_idx].push_back(r.ticket);
+  else s->wbfs_q.push_back(r.ticket);
+  s->pending++;
+  *ticket = r.ticket;
+  s->cv.notify_all();
+  return GBF_OK;
+}
+
+gbf_status gbf_server_poll(gbf_server *s, uint64_t ticket, int32_t *dist_host, int32_t *done,
+                           double *latency_us) {
+  if (!s || !done) return set_error("NULL argument"), GBF_ERR_INVALID;
+  *done = 0;
+  int slot = -1, gi = 0;
+  gbf_status st = GBF_OK;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) return set_error("unknown ticket"), GBF_ERR_NOT_FOUND;
+    Request &r = it->second;
+    if (r.state < 2) return GBF_OK;
+    *done = 1;
+    if (latency_us)
+      *latency_us = std::chrono::duration<double, std::micro>(r.t_done - r.t_submit).count();
+    slot = r.slot;
+    gi = r.graph;
+    st = r.state == 2 ? GBF_OK : r.status;
+    s->reqs.erase(it);
+  }
+  gbf_status cst = GBF_OK;
+  if (st == GBF_OK && dist_host) {
+    cudaError_t e = cudaMemcpy(dist_host, slot_ptr(s, slot), sizeof(int32_t) * (size_t)s->graphs[gi]->n,
+                               cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) cst = cuda_fail(e, "result copy");
+  }
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->free_slots.push_back(slot);
+  }
+  return st != GBF_OK ? st : cst;
+}
+
+gbf_status gbf_server_collect(gbf_server *s, uint64_t *tickets, double *latency_us,
+                              int32_t *status, int32_t cap, int32_t *count) {
+  if (!s || !count || cap < 0 || (cap > 0 && !tickets)) return set_error("bad arguments"), GBF_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(s->mu);
+  int32_t k = 0;
+  for (auto it = s->reqs.begin(); it != s->reqs.end() && k < cap;) {
+    const Request &r = it->second;
+    if (r.state < 2) {
+      ++it;
+      continue;
+    }
+    tickets[k] = r.ticket;
+    if (latency_us) latency_us[k] = std::chrono::duration<double, std::micro>(r.t_done - r.t_submit).count();
+    if (status) status[k] = r.state == 2 ? GBF_OK : r.status;
+    k++;
+    s->free_slots.push_back(r.slot);
+    it = s->reqs.erase(it);
+  }
+  *count = k;
+  return GBF_OK;
+}
+
+gbf_status gbf_server_stats(gbf_server *s, gbf_server_counters *out) {
+  if (!s || !out) return set_error("NULL argument"), GBF_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(s->mu);
+  memset(out, 0, sizeof(*out));
+  out->completed = s->completed;
+  out->failed = s->failed;
+  out->pending = s->pending;
+  out->batches = s->batches;
+  out->batched_queries = s->batched_queries;
+  out->free_slots = s->free_slots.size();
+  out->engines = (int32_t)s->engines.size();
+  return GBF_OK;
+}
+
+gbf_status gbf_server_destroy(gbf_server *s) {
+  if (!s) return GBF_OK;
+  if (s->worker.joinable()) {
+    s->stop.store(true);
+    s->cv.notify_all();
+    s->worker.join();
+  }
+  for (Engine *e : s->engines) destroy_engine(e);
+  if (s->slot_mem) cudaFree(s->slot_mem);
+  delete s;
+  return GBF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,140 @@
+"""GPU tests of the continuous-batching server: every served result equals
+the oracle's answer for that query alone (bit-exact), whatever else was in
+flight; admission refuses work when no result slot is free; batching
+coalesces concurrent BFS queries of a graph."""
+import threading
+
+import numpy as np
+import pytest
+
+import graphgen as G
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gb():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1805_05208_gb300 as gb
+    return gb
+
+
+@pytest.fixture(scope="module")
+def graphs():
+    out = []
+    for sc in (10, 12, 13):
+        out.append(G.add_weights(G.rmat(sc, 16, seed=50 + sc), 1, 22, seed=60 + sc))
+    out.append(G.add_weights(G.grid(40, 50, 0.1, seed=5), 1, 16, seed=6))
+    return out
+
+
+def _drain(gb, srv, tickets, n_of):
+    res = {}
+    pending = dict(tickets)
+    while pending:
+        for t in list(pending):
+            gi = pending[t][0]
+            d = np.empty(n_of[gi], dtype=np.int32)
+            done, lat = gb.gbf_server_poll(srv, t, d)
+            if done:
+                res[t] = (d, lat)
+                del pending[t]
+    return res
+
+
+def _expected(csr, kind, s):
+    return oracle.bfs(csr, s, parents=False)[0] if kind == 0 else oracle.dijkstra(csr, s)
+
+
+@pytest.mark.parametrize("max_batch", [64, 1])
+def test_served_equals_alone(gb, graphs, max_batch):
+    hs = [gb.Graph(c) for c in graphs]
+    srv = gb.gbf_server_create([h.h for h in hs],
+                               gb.gbf_server_options_default(max_batch=max_batch,
+                                                             hbm_budget=64 << 20))
+    rng = np.random.default_rng(7)
+    queries = {}
+    lock = threading.Lock()
+
+    def client(cid):
+        r = np.random.default_rng(100 + cid)
+        for _ in range(60):
+            gi = int(r.integers(len(graphs)))
+            kind = 0 if r.random() < 0.8 else 1
+            s = int(G.sources(graphs[gi], 1, seed=int(r.integers(1 << 30)))[0])
+            t = None
+            while t is None:
+                t = gb.gbf_server_submit(srv, gi, kind, s)
+            with lock:
+                queries[t] = (gi, kind, s)
+
+    th = [threading.Thread(target=client, args=(i,)) for i in range(4)]
+    for x in th:
+        x.start()
+    for x in th:
+        x.join()
+    res = _drain(gb, srv, queries, [c.n for c in graphs])
+    assert len(res) == len(queries) == 240
+    for t, (gi, kind, s) in queries.items():
+        d, lat = res[t]
+        assert lat > 0
+        assert np.array_equal(d, _expected(graphs[gi], kind, s)), (gi, kind, s)
+    st = gb.gbf_server_stats(srv)
+    assert st["completed"] == 240 and st["failed"] == 0 and st["pending"] == 0
+    if max_batch == 1:
+        assert st["batched_queries"] == st["batches"]
+    gb.gbf_server_destroy(srv)
+    del rng
+
+
+def test_coalescing_and_admission(gb, graphs):
+    h = gb.Graph(graphs[2])
+    n = graphs[2].n
+    # room for exactly 100 results
+    budget = 100 * ((n * 4 + 255) // 256 * 256)
+    srv = gb.gbf_server_create([h.h], gb.gbf_server_options_default(hbm_budget=budget,
+                                                                   bfs_engines=1, wbfs_engines=1))
+    srcs = G.sources(graphs[2], 150, seed=9)
+    tickets, busy = [], 0
+    for s in srcs:
+        t = gb.gbf_server_submit(srv, 0, 0, int(s))
+        if t is None:
+            busy += 1
+        else:
+            tickets.append((t, int(s)))
+    assert len(tickets) == 100 and busy == 50          # admission by result slots
+    done = {}
+    while len(done) < len(tickets):
+        for t, s in tickets:
+            if t in done:
+                continue
+            d = np.empty(n, dtype=np.int32)
+            ok, _ = gb.gbf_server_poll(srv, t, d)
+            if ok:
+                done[t] = d
+                assert np.array_equal(d, oracle.bfs(graphs[2], s, parents=False)[0])
+    st = gb.gbf_server_stats(srv)
+    assert st["batches"] < st["batched_queries"]       # queries were coalesced
+    # slots are free again
+    assert gb.gbf_server_submit(srv, 0, 1, int(srcs[0])) is not None
+    with pytest.raises(gb.GbfError):
+        gb.gbf_server_poll(srv, 123456789)
+    gb.gbf_server_destroy(srv)
+
+
+def test_collect_releases(gb, graphs):
+    h = gb.Graph(graphs[0])
+    srv = gb.gbf_server_create([h.h], gb.gbf_server_options_default(hbm_budget=16 << 20))
+    ts = set()
+    for s in G.sources(graphs[0], 50, seed=3):
+        ts.add(gb.gbf_server_submit(srv, 0, 0, int(s)))
+    got = set()
+    while len(got) < len(ts):
+        t, lat, st = gb.gbf_server_collect(srv)
+        assert np.all(st == 0) and np.all(lat > 0)
+        got |= set(int(x) for x in t)
+    assert got == ts
+    gb.gbf_server_destroy(srv)
