@@ -54,6 +54,10 @@ WORKLOADS = {
                               "RMAT scale 24 ef16, autotuned; vs 64 single-source BFS launches"),
     "msbfs-rmat20": dict(kind="msbfs", graph="rmat", scale=20, ef=16, w=None, nsrc=64,
                          desc="multi-source BFS, 64 sources, RMAT scale 20 (profiling size)"),
+    "serve": dict(kind="serve", graph="rmat", scales=(18, 20, 22, 24), ef=16, w=(1, 22), nsrc=0,
+                  rates=(1000, 2000, 5000, 10000, 20000, 50000), warm=2000, meas=20000,
+                  desc="serving: 4 resident RMAT graphs (scales 18/20/22/24, ef16, w in [1,22)), "
+                       "Poisson arrivals, 80% BFS / 20% wBFS, uniform sources with degree > 0"),
     "bfs-grid": dict(kind="bfs", graph="grid", R=4096, C=4096, w=None, nsrc=4,
                      desc="BFS, 4096x4096 grid, 10% edges deleted, source 0 + 3 seeded"),
     "wbfs-grid": dict(kind="wbfs", graph="grid", R=4096, C=4096, w=(1, 16), nsrc=4,
@@ -239,6 +243,131 @@ def run_reference(args, wl, rank, world):
     return 0
 
 
+def serve_run(gb, hs, csrs, opt, rate, n_warm, n_meas, seed):
+    """Offer Poisson arrivals at `rate` q/s to a fresh server; returns
+    (throughput q/s over the measured queries, p50 us, p99 us, stats)."""
+    srv = gb.gbf_server_create([h.h for h in hs], opt)
+    rng = np.random.default_rng(seed)
+    total = n_warm + n_meas
+    gaps = rng.exponential(1.0 / rate, size=total)
+    arrive = np.cumsum(gaps)
+    gi = rng.integers(len(hs), size=total)
+    kind = (rng.random(total) >= 0.8).astype(np.int64)  # 80% BFS, 20% wBFS
+    srcs = np.empty(total, dtype=np.int64)
+    for j in range(len(hs)):
+        idx = np.flatnonzero(gi == j)
+        if idx.size:
+            srcs[idx] = G.sources(csrs[j], idx.size, seed=seed * 7 + j)
+    index = {}
+    lat = np.full(total, np.nan)
+    t_done = np.full(total, np.nan)
+    stop = threading.Event()
+    lock = threading.Lock()
+
+    def collector():
+        while not stop.is_set() or True:
+            t, l, st = gb.gbf_server_collect(srv, 4096)
+            now = time.perf_counter()
+            if len(t):
+                with lock:
+                    for tk, lv in zip(t.tolist(), l.tolist()):
+                        q = index.pop(tk, None)
+                        if q is not None:
+                            lat[q] = lv
+                            t_done[q] = now
+            elif stop.is_set():
+                break
+            else:
+                time.sleep(0.0002)
+
+    th = threading.Thread(target=collector, daemon=True)
+    th.start()
+    t0 = time.perf_counter()
+    i = 0
+    while i < total:
+        now = time.perf_counter() - t0
+        while i < total and arrive[i] <= now:
+            tk = gb.gbf_server_submit(srv, int(gi[i]), int(kind[i]), int(srcs[i]))
+            if tk is None:          # not admissible now: offered again shortly
+                break
+            with lock:
+                index[tk] = i
+            i += 1
+        else:
+            time.sleep(0.00005)
+            continue
+        time.sleep(0.0001)
+    # wait for completion
+    while True:
+        with lock:
+            left = len(index)
+        if left == 0:
+            break
+        time.sleep(0.001)
+    stop.set()
+    th.join()
+    st = gb.gbf_server_stats(srv)
+    gb.gbf_server_destroy(srv)
+    m = slice(n_warm, total)
+    ml = lat[m]
+    t_first = t0 + arrive[n_warm]
+    thr = n_meas / (np.nanmax(t_done[m]) - t_first)
+    return float(thr), float(np.nanpercentile(ml, 50)), float(np.nanpercentile(ml, 99)), st
+
+
+def run_serve(args, wl, rank, world):
+    """Serving workload: batched server vs one-query-per-launch FIFO."""
+    import torch
+    import paper_1805_05208_gb300 as gb
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(0)
+    csrs = []
+    for sc in wl["scales"]:
+        g = G.rmat(sc, wl["ef"], 0.57, 0.19, 0.19, seed=1, permute=True)
+        G.add_weights(g, wl["w"][0], wl["w"][1], seed=2)
+        csrs.append(g)
+    hs = [gb.Graph(c, validate=gb.VALIDATE_BASIC) for c in csrs]
+    rates = [int(r) for r in (args.rates.split(",") if args.rates else wl["rates"])]
+    warm, meas = (args.serve_warm or wl["warm"]), (args.serve_meas or wl["meas"])
+    modes = {
+        "batched": gb.gbf_server_options_default(bfs_engines=2, wbfs_engines=2, max_batch=64),
+        "one_per_launch_fifo": gb.gbf_server_options_default(bfs_engines=1, wbfs_engines=1,
+                                                             max_batch=1),
+    }
+    res = {}
+    with ClockSampler(0) as clk:
+        for name, opt in modes.items():
+            res[name] = []
+            for r in rates:
+                thr, p50, p99, st = serve_run(gb, hs, csrs, opt, r, warm, meas, seed=4)
+                res[name].append({"offered_qps": r, "qps": thr, "p50_us": p50, "p99_us": p99,
+                                  "mean_batch": st["batched_queries"] / max(1, st["batches"]),
+                                  "failed": st["failed"]})
+    best = max(x["qps"] for x in res["batched"])
+    base = max(x["qps"] for x in res["one_per_launch_fifo"])
+    clocks = clk.summary()
+    line = {
+        "metric": "served queries/s", "value": best, "unit": "queries/s", "n_gpus": 1,
+        "steps": len(rates), "warmup": warm, "ms_per_step": None, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": "serve", "desc": wl["desc"], "rates": rates,
+                   "queries_per_rate": {"warmup": warm, "measured": meas},
+                   "graphs": [{"scale": sc, "n": c.n, "arcs": c.m} for sc, c in zip(wl["scales"], csrs)],
+                   "arrival_seed": 4},
+        "serve": res,
+        "speedup_vs_one_per_launch": best / base,
+        "e2e": {"value": best, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+                "note": "submit-to-completion through the C ABI; results left on the device"},
+        "gpu_launches": None,
+        "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+    }
+    print(json.dumps(line))
+    for h in hs:
+        h.close()
+    return 0
+
+
 def run_msbfs(args, wl, g, srcs, graph, opt, stream, dev, rank, world, barrier, dist_mod):
     """One step = one multi-source BFS launch over the 64 sources; the same
     64 sources as single-source launches are timed beside it."""
@@ -371,6 +500,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--opt", default="", help="comma list of gbf_options overrides k=v")
+    ap.add_argument("--rates", default="", help="serve: comma list of offered rates (q/s)")
+    ap.add_argument("--serve-warm", type=int, default=0)
+    ap.add_argument("--serve-meas", type=int, default=0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     wl = WORKLOADS[args.workload]
@@ -381,6 +513,8 @@ def main():
 
     if args.impl == "reference":
         return run_reference(args, wl, rank, world)
+    if wl["kind"] == "serve":
+        return run_serve(args, wl, rank, world)
 
     import torch
     import torch.distributed as dist_mod

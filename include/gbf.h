@@ -72,14 +72,17 @@ typedef struct gbf_graph gbf_graph;
  *                 out-degree sum exceeds m / pull_divisor (default 20; -1 = push only)
  *   heavy_cutoff  largest number of frontier edges one CTA processes as one
  *                 block of the blocked sparse edgeMap; a vertex with more
- *                 edges is split over several CTAs (power of two, 256..4096, default 512)
+ *                 edges is split over several CTAs (power of two, 256..4096; 0 = per-query
+ *                 default: 1024 for multi-source BFS, 512 for BFS and wBFS, whose
+ *                 light vertices (<= heavy_cutoff / 8 arcs) are expanded without it)
  *   bucket_window number of open buckets nB of the wBFS bucket structure
  *                 (1..256, default min(max weight + 1, 256); values <= max weight use the overflow bucket)
  *   dense_wbfs    1 = let wBFS switch to a dense edgeMap for dense buckets (default 0)
  *   spin_cap_us   time limit of every bounded device wait, microseconds (default 5,000,000)
  *   counters      reserved (statistics are always collected)
  *   ctas          CTAs of the persistent kernels (default: every CTA that fits, all SMs)
- *   pull_serial   neighbours a thread scans alone before the dense step hands a vertex to its whole warp (default 8)
+ *   pull_serial   arcs each vertex checks on its own (4 at a time) before the dense step
+ *                 walks its remaining arcs with the whole warp (default 8)
  *   inject_wait   fault injection for tests: 1 = one CTA waits on a flag nothing sets,
  *                 so the first grid barrier times out and the call returns GBF_ERR_TIMEOUT
  */

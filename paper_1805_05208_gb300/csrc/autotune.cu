@@ -136,7 +136,7 @@ extern "C" gbf_status gbf_autotune(gbf_graph *h, int32_t kind, gbf_options *out)
 
   // median time of one configuration (ms); +inf if it fails
   auto measure = [&](const gbf_options &opt, float *ms_out) -> gbf_status {
-    const Opts o = resolve(&opt, g);
+    const Opts o = resolve(&opt, g, kind);
     std::vector<float> t;
     for (int si = 0; si < nsrc; si++) {
       for (int r = 0; r < reps + 1; r++) {
@@ -166,6 +166,7 @@ extern "C" gbf_status gbf_autotune(gbf_graph *h, int32_t kind, gbf_options *out)
 
   gbf_options best;
   gbf_options_default(&best);
+  best.heavy_cutoff = resolve(&best, g, kind).heavy_cutoff;  // the kind's default, explicit
   float best_ms = 0;
   s = measure(best, &best_ms);
   if (s == GBF_OK) {

@@ -94,7 +94,13 @@ struct BfsPushFn {
   }
 };
 
-// Dense direction: one warp per 32-vertex word of the bitmaps.
+// Dense direction: one warp per 32-vertex word of the bitmaps.  Each
+// unvisited vertex checks its first arcs (4 at a time, loads batched); the
+// warp then walks the remaining arcs of every still-unresolved vertex of the
+// word together, 32 consecutive arcs per window and kU windows per step,
+// dropping a vertex as soon as one of its arcs hits the frontier.  Arcs are
+// taken in CSR order and the first hit becomes the parent, as in a
+// sequential early-exit scan.
 __device__ void pull_level(const BfsParams &P, const uint32_t *fin, uint32_t *fout, int32_t level,
                            unsigned long long *counter, unsigned long long &scanned,
                            unsigned long long &reached, unsigned long long &cand_cnt,
@@ -104,6 +110,7 @@ __device__ void pull_level(const BfsParams &P, const uint32_t *fin, uint32_t *fo
   const uint32_t nwords = ((uint32_t)g.n + 31) >> 5;
   const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t tw = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t first = (uint32_t)P.pull_serial;
   uint32_t my_cnt = 0, my_deg = 0;
   for (uint32_t wi = gw; wi < nwords; wi += tw) {
     const uint32_t vis = P.visited[wi];
@@ -117,46 +124,76 @@ __device__ void pull_level(const BfsParams &P, const uint32_t *fin, uint32_t *fo
       cand_cnt++;
     }
     int32_t par = -1;
+    // pass 1: the first arcs of each candidate, four loads in flight per lane
     uint32_t k = s;
-    if (cand) {
-      const uint32_t lim = min(e, s + (uint32_t)P.pull_serial);
-      for (; k < lim; k++) {
-        const int32_t u = __ldg(g.tgt + k);
-        if ((fin[u >> 5] >> (u & 31)) & 1u) {
-          par = u;
-          k++;
-          break;
-        }
+    for (uint32_t c = 0; c < first; c += 4) {
+      int32_t u[4];
+      bool h[4];
+#pragma unroll
+      for (int r = 0; r < 4; r++) {
+        const uint32_t kk = k + r;
+        u[r] = (cand && par < 0 && kk < e) ? __ldg(g.tgt + kk) : -1;
       }
-      scanned += k - s;
+#pragma unroll
+      for (int r = 0; r < 4; r++) h[r] = u[r] >= 0 && ((fin[u[r] >> 5] >> (u[r] & 31)) & 1u);
+      if (cand && par < 0) {
+        uint32_t used = min(4u, e - min(k, e));
+#pragma unroll
+        for (int r = 3; r >= 0; r--)
+          if (h[r]) {
+            par = u[r];
+            used = (uint32_t)r + 1;
+          }
+        scanned += used;
+        k += used;
+      }
     }
-    unsigned rm = __ballot_sync(kFull, cand && par < 0 && k < e);
-    while (rm) {
-      const int l = __ffs(rm) - 1;
-      rm &= rm - 1;
-      const uint32_t ks = __shfl_sync(kFull, k, l), ke = __shfl_sync(kFull, e, l);
-      int32_t found = -1;
-      uint32_t looked = 0;
-      for (uint32_t b = ks; b < ke; b += 32) {
-        const uint32_t kk = b + lane;
-        bool hit = false;
-        int32_t u = 0;
-        if (kk < ke) {
-          u = __ldg(g.tgt + kk);
-          hit = (fin[u >> 5] >> (u & 31)) & 1u;
+    // pass 2: the remaining arcs of the unresolved candidates, warp windows
+    const uint32_t rem = (cand && par < 0 && k < e) ? e - k : 0u;
+    uint32_t incl = rem;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
+    const uint32_t excl = incl - rem;
+    unsigned pending = __ballot_sync(kFull, rem > 0);
+    for (uint32_t w0 = 0; w0 < total && pending; w0 += 32 * kU) {
+      int32_t uu[kU];
+      int own[kU];
+      bool hit[kU];
+#pragma unroll
+      for (int r = 0; r < kU; r++) {
+        const uint32_t ee = w0 + 32 * r + lane;
+        int o = 0;
+#pragma unroll
+        for (int st = 16; st > 0; st >>= 1) {
+          const uint32_t cv = __shfl_sync(kFull, incl, o + st - 1);
+          if (cv <= ee) o += st;
         }
-        const unsigned hb = __ballot_sync(kFull, hit);
-        if (hb) {
-          const int f = __ffs(hb) - 1;
-          found = __shfl_sync(kFull, u, f);
-          looked += (uint32_t)f + 1;
-          break;
-        }
-        looked += min(32u, ke - b);
+        o = min(o, 31);
+        const uint32_t eo = __shfl_sync(kFull, excl, o);
+        const uint32_t ko = __shfl_sync(kFull, k, o);
+        const bool val = ee < total && ((pending >> o) & 1u);
+        own[r] = o;
+        uu[r] = val ? __ldg(g.tgt + ko + (ee - eo)) : -1;
       }
-      if (lane == l) {
-        par = found;
-        scanned += looked;
+#pragma unroll
+      for (int r = 0; r < kU; r++) hit[r] = uu[r] >= 0 && ((fin[uu[r] >> 5] >> (uu[r] & 31)) & 1u);
+#pragma unroll
+      for (int r = 0; r < kU; r++) {
+        const unsigned lb = __ballot_sync(kFull, uu[r] >= 0);
+        if (lane == 0) scanned += __popc(lb);
+        unsigned hb = __ballot_sync(kFull, hit[r]);
+        while (hb) {
+          const int f = __ffs(hb) - 1;
+          const int o = __shfl_sync(kFull, own[r], f);
+          const int32_t uf = __shfl_sync(kFull, uu[r], f);
+          if (lane == o && par < 0) par = uf;
+          hb &= ~__ballot_sync(kFull, hit[r] && own[r] == o);
+          pending &= ~(1u << o);
+        }
       }
     }
     const bool got = par >= 0;
@@ -369,6 +406,17 @@ gbf_status launch_bfs(Graph &g, Workspace &ws, int32_t src, int32_t *dist, int32
   ws.last_grid = grid;
   ws.last_block = o.block;
   return GBF_OK;
+}
+
+int resident_ctas_per_sm_bfs(const Opts &o) {
+  const size_t smem = push_smem_bytes(SmemShape{o.heavy_cutoff, 2 * kU * o.block, 0, 0});
+  if (cudaFuncSetAttribute(bfs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return 0;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bfs_kernel, o.block, smem) != cudaSuccess)
+    return 0;
+  return per_sm;
 }
 
 }  // namespace gbf

@@ -275,7 +275,7 @@ struct QueueOut {
 // (multiple of 256 edges) falling in an entry's range records the entry.
 __device__ __forceinline__ void stage_flush(PushSmem &S, const QueueOut &out, Ctl *ctl) {
   __syncthreads();
-  const uint32_t k = S.misc[0];
+  const uint32_t k = min(S.misc[0], S.cap_out);  // entries beyond cap were spilled
   if (k == 0) return;
   const uint32_t tid = threadIdx.x, bd = blockDim.x;
   const uint32_t per = (k + bd - 1) / bd;
@@ -304,12 +304,22 @@ __device__ __forceinline__ void stage_flush(PushSmem &S, const QueueOut &out, Ct
   if (S.misc[3] == 0) {
     const uint32_t pos = S.misc[1], dpos = S.misc[2];
     for (uint32_t i = tid; i < k; i += bd) {
-      uint32_t a = dpos + S.pref[i], d = S.out_d[i];
       out.q[pos + i] = S.out_v[i];
-      out.qoff[pos + i] = a;
-      for (uint32_t c = (a + kFine - 1) >> kFineLog; (c << kFineLog) < a + d; c++) {
-        if (c < out.cs_cap) out.cs[c] = pos + i;
+      out.qoff[pos + i] = dpos + S.pref[i];
+    }
+    // chunk starts (multiples of 256) inside [dpos, dpos + total), spread over
+    // the CTA: each finds its entry by binary search of the staged prefix
+    const uint32_t c0 = (dpos + kFine - 1) >> kFineLog;
+    const uint32_t c1 = (uint32_t)(((unsigned long long)dpos + total + kFine - 1) >> kFineLog);
+    for (uint32_t c = c0 + tid; c < c1; c += bd) {
+      const uint32_t rel = (c << kFineLog) - dpos;
+      uint32_t lo = 0, hi = k;  // largest i with pref[i] <= rel
+      while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (S.pref[mid] <= rel) lo = mid;
+        else hi = mid;
       }
+      if (c < out.cs_cap) out.cs[c] = pos + lo;
     }
   }
   __syncthreads();
@@ -343,8 +353,9 @@ __device__ __forceinline__ uint32_t smem_upper(const uint32_t *base, uint32_t nv
 // contiguous run of K windows of 32 consecutive edges (coalesced target
 // loads); it locates the vertex of each lane from the boundaries falling in
 // the window (one shared load per lane and a warp OR).  Every step hands kU
-// windows to fn.batch (which issues all their loads before using them) and
-// then runs sink.step_done, where the CTA may flush its staging buffers.
+// windows to fn.batch, which issues all their loads before using them.
+// Warps do not synchronise inside the walk: appends that find the shared
+// staging buffer full take the sink's direct path to global memory.
 template <class Fn, class Sink>
 __device__ __forceinline__ void walk_chunk(PushSmem &S, uint32_t m, uint32_t nv, uint32_t e_lo,
                                            uint32_t e_hi, Fn &fn, Sink &sink) {
@@ -388,7 +399,6 @@ __device__ __forceinline__ void walk_chunk(PushSmem &S, uint32_t m, uint32_t nv,
       }
     }
     fn.batch(val, uu, idx, sink, S);
-    sink.step_done(S);
   }
 }
 
@@ -422,7 +432,39 @@ __device__ __forceinline__ void blocked_edge_map(const DevGraph &g, const QueueI
     if (threadIdx.x == 0) S.base[nv] = (i1 + 1 < in.cnt) ? in.qoff[i1 + 1] : in.D;
     __syncthreads();
     walk_chunk(S, g.m, nv, e_lo, e_hi, fn, sink);
+    sink.chunk_end(S);
   }
+}
+
+// Warp-collective: stage the lanes with emit set; an entry that finds the
+// stage full is written straight to the output queue (reserving its own
+// count and edge range, then its chunk starts).
+__device__ __forceinline__ void stage_append_or_spill(PushSmem &S, bool emit, int32_t v,
+                                                      uint32_t d, const QueueOut &out, Ctl *ctl) {
+  const unsigned bal = __ballot_sync(kFull, emit);
+  if (bal == 0) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(bal) - 1;
+  uint32_t pos = 0;
+  if (lane == leader) pos = atomicAdd(&S.misc[0], (uint32_t)__popc(bal));
+  pos = __shfl_sync(kFull, pos, leader);
+  if (!emit) return;
+  const uint32_t r = pos + __popc(bal & lanemask_lt());
+  if (r < S.cap_out) {
+    S.out_v[r] = v;
+    S.out_d[r] = d;
+    return;
+  }
+  const unsigned long long old = atomicAdd(out.counter, (1ull << 32) | d);
+  const uint32_t qp = (uint32_t)(old >> 32), a = (uint32_t)old;
+  if (qp >= out.q_cap) {
+    raise_error(ctl, GBF_ERR_OVERFLOW, 11);
+    return;
+  }
+  out.q[qp] = v;
+  out.qoff[qp] = a;
+  for (uint32_t c = (a + kFine - 1) >> kFineLog; (c << kFineLog) < a + d; c++)
+    if (c < out.cs_cap) out.cs[c] = qp;
 }
 
 // Sink that stages into shared memory and flushes into a QueueOut.
@@ -430,11 +472,12 @@ struct StagedSink {
   QueueOut out;
   Ctl *ctl;
   __device__ __forceinline__ void append(PushSmem &S, bool emit, int32_t v, uint32_t d) {
-    stage_append(S, emit, v, d);
+    stage_append_or_spill(S, emit, v, d, out, ctl);
   }
-  __device__ __forceinline__ void step_done(PushSmem &S) {
+  // CTA-collective, between chunks
+  __device__ __forceinline__ void chunk_end(PushSmem &S) {
     __syncthreads();
-    if (S.misc[0] + kU * blockDim.x > S.cap_out) stage_flush(S, out, ctl);
+    if (S.misc[0] > (S.cap_out >> 1)) stage_flush(S, out, ctl);
   }
   __device__ __forceinline__ void finish(PushSmem &S) { stage_flush(S, out, ctl); }
 };

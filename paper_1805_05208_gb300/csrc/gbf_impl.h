@@ -130,7 +130,7 @@ struct Opts {
   int block, pull_divisor, heavy_cutoff, bucket_window, dense_wbfs, ctas, pull_serial, inject_wait;
   long long spin_cap_ns;
 };
-Opts resolve(const gbf_options *o, const Graph &g);
+Opts resolve(const gbf_options *o, const Graph &g, int kind);  // kind: GBF_TUNE_*
 
 // Workspace management (graph.cu)
 gbf_status ws_ensure_base(Graph &g, Workspace &ws);
@@ -146,6 +146,10 @@ gbf_status launch_wbfs(Graph &g, Workspace &ws, int32_t src, int32_t *dist, cons
                        cudaStream_t st);
 gbf_status launch_msbfs(Graph &g, Workspace &ws, const int32_t *srcs_host, int32_t k,
                         int32_t *dist, const Opts &o, cudaStream_t st);
+// Resident CTAs per SM of each persistent kernel for these knobs (0 on error).
+int resident_ctas_per_sm_bfs(const Opts &o);
+int resident_ctas_per_sm_wbfs(const Opts &o, int nB);
+int resident_ctas_per_sm_msbfs(const Opts &o);
 gbf_status launch_msbfs_rows(Graph &g, Workspace &ws, const int32_t *srcs_host, int32_t k,
                              int32_t *const *rows, const Opts &o, cudaStream_t st);
 

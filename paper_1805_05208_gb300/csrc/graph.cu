@@ -28,7 +28,7 @@ gbf_status cuda_fail(cudaError_t e, const char *what) {
 }
 
 // ------------------------------------------------------------------ options
-Opts resolve(const gbf_options *o, const Graph &g) {
+Opts resolve(const gbf_options *o, const Graph &g, int kind) {
   (void)g;
   gbf_options d;
   gbf_options_default(&d);
@@ -37,7 +37,9 @@ Opts resolve(const gbf_options *o, const Graph &g) {
   r.block = o->block ? o->block : d.block;
   if (r.block != 128 && r.block != 256 && r.block != 512 && r.block != 1024) r.block = d.block;
   r.pull_divisor = o->pull_divisor ? o->pull_divisor : d.pull_divisor;
-  r.heavy_cutoff = o->heavy_cutoff ? o->heavy_cutoff : d.heavy_cutoff;
+  // heavy_cutoff 0: per-kind default
+  r.heavy_cutoff = o->heavy_cutoff ? o->heavy_cutoff
+                                   : (kind == GBF_TUNE_MSBFS ? 1024 : 512);
   int hc = 256;
   while (hc < r.heavy_cutoff && hc < 4096) hc <<= 1;
   r.heavy_cutoff = std::max(hc, r.block);  // staging buffer must hold one CTA pass
@@ -312,7 +314,7 @@ gbf_status gbf_options_default(gbf_options *opt) {
   memset(opt, 0, sizeof(*opt));
   opt->block = 256;
   opt->pull_divisor = 20;
-  opt->heavy_cutoff = 512;
+  opt->heavy_cutoff = 0;
   opt->bucket_window = 0;
   opt->dense_wbfs = 0;
   opt->spin_cap_us = 5000000;
@@ -463,7 +465,7 @@ gbf_status gbf_bfs(gbf_graph *h, int32_t src, int32_t *dist, int32_t *parent, in
   cudaStream_t st = (cudaStream_t)cuda_stream;
   std::lock_guard<std::mutex> lk(g.mu);
   GBF_TRY(ws_ensure_base(g, g.ws));
-  const Opts o = resolve(opt, g);
+  const Opts o = resolve(opt, g, GBF_TUNE_BFS);
   int32_t *dd = mem == GBF_HOST ? g.ws.dist_tmp : dist;
   int32_t *pp = parent ? (mem == GBF_HOST ? g.ws.parent_tmp : parent) : nullptr;
   GBF_TRY(launch_bfs(g, g.ws, src, dd, pp, o, st));
@@ -483,7 +485,7 @@ gbf_status gbf_wbfs(gbf_graph *h, int32_t src, int32_t *dist, int mem, const gbf
   if (mem != GBF_HOST && mem != GBF_DEVICE) return set_error("bad mem"), GBF_ERR_INVALID;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   std::lock_guard<std::mutex> lk(g.mu);
-  const Opts o = resolve(opt, g);
+  const Opts o = resolve(opt, g, GBF_TUNE_WBFS);
   int nB = o.bucket_window > 0 ? o.bucket_window : (int)std::max<uint32_t>(g.w_max + 1, 2);
   nB = std::min(nB, 256);
   GBF_TRY(ws_ensure_wbfs(g, g.ws, nB));
@@ -520,7 +522,7 @@ gbf_status gbf_msbfs(gbf_graph *h, const int32_t *srcs, int32_t k, int32_t *dist
   cudaStream_t st = (cudaStream_t)cuda_stream;
   std::lock_guard<std::mutex> lk(g.mu);
   GBF_TRY(ws_ensure_msbfs(g, g.ws, mem == GBF_HOST));
-  const Opts o = resolve(opt, g);
+  const Opts o = resolve(opt, g, GBF_TUNE_MSBFS);
   int32_t *dd = mem == GBF_HOST ? g.ws.ms_dist_tmp : dist;
   GBF_TRY(launch_msbfs(g, g.ws, srcs, k, dd, o, st));
   if (mem == GBF_DEVICE) return GBF_OK;

@@ -100,7 +100,7 @@ struct TouchSink {
       else raise_error(ctl, GBF_ERR_OVERFLOW, 10);
     }
   }
-  __device__ __forceinline__ void step_done(PushSmem &) { __syncthreads(); }
+  __device__ __forceinline__ void chunk_end(PushSmem &) { __syncthreads(); }
 };
 
 // Push Update for kU windows: lanes visit[u] & ~seen[v] are OR-ed into next[v].
@@ -437,6 +437,17 @@ gbf_status launch_msbfs(Graph &g, Workspace &ws, const int32_t *srcs_host, int32
   int32_t *rows[64];
   for (int i = 0; i < 64; i++) rows[i] = i < k ? dist + (size_t)i * (size_t)g.n : nullptr;
   return launch_msbfs_rows(g, ws, srcs_host, k, rows, o, st);
+}
+
+int resident_ctas_per_sm_msbfs(const Opts &o) {
+  const size_t smem = push_smem_bytes(SmemShape{o.heavy_cutoff, 2 * kU * o.block, 0, 0});
+  if (cudaFuncSetAttribute(msbfs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return 0;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, msbfs_kernel, o.block, smem) != cudaSuccess)
+    return 0;
+  return per_sm;
 }
 
 }  // namespace gbf

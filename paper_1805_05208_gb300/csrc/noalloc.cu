@@ -120,7 +120,7 @@ extern "C" gbf_status gbf_bfs_noalloc(int32_t n, uint32_t m, const uint32_t *off
   ws.n = n;
   ws.m = m;
 
-  const Opts o = resolve(opt, g);
+  const Opts o = resolve(opt, g, GBF_TUNE_BFS);
   cudaStream_t st = (cudaStream_t)cuda_stream;
   s = launch_bfs(g, ws, src, dist, parent, o, st);
   if (s != GBF_OK) return s;

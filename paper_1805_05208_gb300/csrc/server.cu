@@ -313,14 +313,21 @@ gbf_status gbf_server_create(gbf_graph *const *graphs, int32_t ngraphs,
     else st = ws_ensure_base(sh, en->ws);
     if (st != GBF_OK) return fail(st);
   }
-  // kernel knobs: an equal CTA share per engine (all engines co-resident)
+  // kernel knobs: every engine gets an equal share of the CTAs the GPU can
+  // hold at once (the smallest residency among the kernels in use), so all
+  // engines' persistent launches are co-resident whatever runs together
   gbf_options ko = s->opt.kernel;
-  s->kopt_bfs = resolve(&ko, *s->graphs[0]);
-  s->kopt_wbfs = s->kopt_bfs;
+  s->kopt_bfs = resolve(&ko, *s->graphs[0], s->opt.max_batch > 1 ? GBF_TUNE_MSBFS : GBF_TUNE_BFS);
+  s->kopt_wbfs = resolve(&ko, *s->graphs[0], GBF_TUNE_WBFS);
   {
-    // resident CTAs per SM for the default block size is at least 1; a share
-    // of num_sms * 2 / engines keeps every engine resident even at 2 CTAs/SM
-    const int share = std::max(1, (sms * 2) / nengines);
+    int per_sm = s->opt.max_batch > 1 ? resident_ctas_per_sm_msbfs(s->kopt_bfs)
+                                      : resident_ctas_per_sm_bfs(s->kopt_bfs);
+    if (any_w && s->opt.wbfs_engines > 0) {
+      const int nB = (int)std::min<uint32_t>(std::max<uint32_t>(max_w + 1, 2), 256);
+      per_sm = std::min(per_sm, resident_ctas_per_sm_wbfs(s->kopt_wbfs, nB));
+    }
+    if (per_sm < 1) return fail((set_error("kernels do not fit on an SM"), GBF_ERR_INVALID));
+    const int share = std::max(1, (sms * per_sm) / nengines);
     if (s->kopt_bfs.ctas == 0 || s->kopt_bfs.ctas > share) s->kopt_bfs.ctas = share;
     if (s->kopt_wbfs.ctas == 0 || s->kopt_wbfs.ctas > share) s->kopt_wbfs.ctas = share;
   }

@@ -95,21 +95,40 @@ struct FileSink {
     uint32_t pos = 0;
     if (lane == leader) pos = atomicAdd(&S.misc[4], (uint32_t)__popc(bal));
     pos = __shfl_sync(kFull, pos, leader);
-    if (low) {
-      const int32_t nd = (int32_t)ndu;
-      const uint32_t r = pos + __popc(bal & lanemask_lt());
+    if (!low) return;
+    const int32_t nd = (int32_t)ndu;
+    const int32_t sl = (P->slide || nd < lo + P->nB) ? nd % P->nB : -nd - 2;
+    const uint32_t r = pos + __popc(bal & lanemask_lt());
+    if (r < S.cap_out) {
       S.fv[r] = v;
-      S.fs[r] = (P->slide || nd < lo + P->nB) ? nd % P->nB : -nd - 2;
+      S.fs[r] = sl;
+      return;
     }
+    // the stage is full: file this entry directly
+    if (sl >= 0) {
+      const uint32_t gp = atomicAdd(P->slot_cnt + sl, 1u) % (uint32_t)P->g.n;
+      P->slots[(size_t)sl * (size_t)P->g.n + gp] = v;
+      atomicOr(imask + (sl >> 5), 1u << (sl & 31));
+    } else {
+      const uint32_t gp = atomicAdd(&P->ctl->ovf_cnt[cur], 1u);
+      if (gp < P->ovf_cap) {
+        P->ovf[cur][gp] = make_int2(v, nd);
+        atomicMin(&P->ctl->ovf_min[cur], nd);
+      } else {
+        raise_error(P->ctl, GBF_ERR_OVERFLOW, 12);
+      }
+    }
+    c->inserts++;
   }
-  __device__ __forceinline__ void step_done(PushSmem &S) {
+  // CTA-collective, between chunks / loop iterations.
+  __device__ __forceinline__ void chunk_end(PushSmem &S) {
     __syncthreads();
-    if (S.misc[4] + kU * blockDim.x > S.cap_out) flush(S);
+    if (S.misc[4] > (S.cap_out >> 1)) flush(S);
   }
   // CTA-collective.
   __device__ void flush(PushSmem &S) {
     __syncthreads();
-    const uint32_t k = S.misc[4];
+    const uint32_t k = min(S.misc[4], S.cap_out);  // entries beyond cap were filed directly
     if (k == 0) return;
     const int nB = P->nB;
     const uint32_t n = (uint32_t)P->g.n;
@@ -248,7 +267,7 @@ __device__ void dense_round(const WbfsParams &P, int32_t b, PushSmem &S, FileSin
       c.relax++;
     }
     sink.append(S, low, v, (uint32_t)best);
-    sink.step_done(S);
+    sink.chunk_end(S);
   }
   sink.flush(S);
 }
@@ -349,7 +368,7 @@ __global__ void __launch_bounds__(1024) wbfs_kernel(WbfsParams P) {
         const int2 e = valid ? P.ovf[cur][i] : make_int2(0, 0);
         const bool live = valid && P.dist[e.x] == e.y;
         fs.append(S, live, e.x, (uint32_t)e.y);
-        fs.step_done(S);
+        fs.chunk_end(S);
       }
       fs.flush(S);
       lo = nlo;
@@ -428,6 +447,7 @@ __global__ void __launch_bounds__(1024) wbfs_kernel(WbfsParams P) {
       }
       __syncthreads();
       walk_chunk(S, g.m, nv, 0u, E, fn, fsink);
+      fsink.chunk_end(S);
       if (S.misc[0] + blockDim.x > S.cap_out) stage_flush(S, fout, ctl);
     }
     stage_flush(S, fout, ctl);
@@ -519,6 +539,18 @@ gbf_status launch_wbfs(Graph &g, Workspace &ws, int32_t src, int32_t *dist, cons
   ws.last_grid = grid;
   ws.last_block = o.block;
   return GBF_OK;
+}
+
+int resident_ctas_per_sm_wbfs(const Opts &o, int nB) {
+  const size_t smem = push_smem_bytes(SmemShape{o.heavy_cutoff, 2 * kU * o.block, 1, nB}) +
+                      sizeof(uint32_t) * (size_t)nB;
+  if (cudaFuncSetAttribute(wbfs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess)
+    return 0;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wbfs_kernel, o.block, smem) != cudaSuccess)
+    return 0;
+  return per_sm;
 }
 
 }  // namespace gbf
