@@ -65,6 +65,17 @@ WORKLOADS = {
 }
 
 
+def reduce_job(ms, te, dist_mod, device):
+    """Whole-job timing across ranks: the slowest rank's time and the sum of
+    the traversed edges (queries are sharded across ranks, no data exchange)."""
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist_mod.all_reduce(t, op=dist_mod.ReduceOp.MAX)
+    e = torch.tensor([float(te)], dtype=torch.float64, device=device)
+    dist_mod.all_reduce(e, op=dist_mod.ReduceOp.SUM)
+    return float(t.item()), float(e.item())
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -421,12 +432,7 @@ def run_msbfs(args, wl, g, srcs, graph, opt, stream, dev, rank, world, barrier, 
     torch.cuda.synchronize()
     ms_single64 = a0.elapsed_time(a1)
     if world > 1:
-        t = torch.tensor([ms_total], device=dev)
-        dist_mod.all_reduce(t, op=dist_mod.ReduceOp.MAX)
-        ms_total = float(t.item())
-        tt = torch.tensor([float(te_step)], device=dev, dtype=torch.float64)
-        dist_mod.all_reduce(tt)
-        te_all = float(tt.item())
+        ms_total, te_all = reduce_job(ms_total, te_step, dist_mod, dev)
     else:
         te_all = float(te_step)
     value = te_all * args.steps / (ms_total / 1e3) / 1e9
@@ -586,12 +592,7 @@ def main():
         raise RuntimeError(f"device error {st_last['device_error']}")
     ms_total = t_start.elapsed_time(t_end)
     if world > 1:
-        t = torch.tensor([ms_total], device=dev)
-        dist_mod.all_reduce(t, op=dist_mod.ReduceOp.MAX)
-        ms_total = float(t.item())
-        tt = torch.tensor([float(te_step)], device=dev, dtype=torch.float64)
-        dist_mod.all_reduce(tt)
-        te_all = float(tt.item())
+        ms_total, te_all = reduce_job(ms_total, te_step, dist_mod, dev)
     else:
         te_all = float(te_step)
     launch_ms = [e[0].elapsed_time(e[1]) for e in ev]

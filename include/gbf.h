@@ -67,7 +67,8 @@ typedef struct gbf_graph gbf_graph;
 /*
  * Tuning knobs.  Zero in any field selects the default; results (distances)
  * never depend on them.  gbf_options_default() fills the defaults.
- *   block         threads per CTA of the persistent kernels: 128, 256, 512 or 1024 (default 256)
+ *   block         threads per CTA of the persistent kernels: 128, 256, 512 or 1024
+ *                 (0 = per-query default: 512 for wBFS, 256 otherwise)
  *   pull_divisor  edgeMap takes the dense (pull) direction when the frontier's
  *                 out-degree sum exceeds m / pull_divisor (default 20; -1 = push only)
  *   heavy_cutoff  largest number of frontier edges one CTA processes as one

@@ -166,7 +166,11 @@ extern "C" gbf_status gbf_autotune(gbf_graph *h, int32_t kind, gbf_options *out)
 
   gbf_options best;
   gbf_options_default(&best);
-  best.heavy_cutoff = resolve(&best, g, kind).heavy_cutoff;  // the kind's default, explicit
+  {
+    const Opts d0 = resolve(&best, g, kind);  // the kind's defaults, made explicit
+    best.heavy_cutoff = d0.heavy_cutoff;
+    best.block = d0.block;
+  }
   float best_ms = 0;
   s = measure(best, &best_ms);
   if (s == GBF_OK) {

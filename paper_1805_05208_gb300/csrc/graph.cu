@@ -34,8 +34,11 @@ Opts resolve(const gbf_options *o, const Graph &g, int kind) {
   gbf_options_default(&d);
   if (!o) o = &d;
   Opts r;
-  r.block = o->block ? o->block : d.block;
-  if (r.block != 128 && r.block != 256 && r.block != 512 && r.block != 1024) r.block = d.block;
+  // block 0: per-kind default (wBFS gains from wider CTAs: fewer barrier
+  // arrivals per round and more warps per chunk)
+  const int kind_block = kind == GBF_TUNE_WBFS ? 512 : 256;
+  r.block = o->block ? o->block : kind_block;
+  if (r.block != 128 && r.block != 256 && r.block != 512 && r.block != 1024) r.block = kind_block;
   r.pull_divisor = o->pull_divisor ? o->pull_divisor : d.pull_divisor;
   // heavy_cutoff 0: per-kind default
   r.heavy_cutoff = o->heavy_cutoff ? o->heavy_cutoff
@@ -312,7 +315,7 @@ extern "C" {
 gbf_status gbf_options_default(gbf_options *opt) {
   if (!opt) return GBF_ERR_INVALID;
   memset(opt, 0, sizeof(*opt));
-  opt->block = 256;
+  opt->block = 0;
   opt->pull_divisor = 20;
   opt->heavy_cutoff = 0;
   opt->bucket_window = 0;
