@@ -379,7 +379,7 @@ gbf_status launch_bfs(Graph &g, Workspace &ws, int32_t src, int32_t *dist, int32
   P.trace_cap = ws.trace_cap;
   P.pull_divisor = o.pull_divisor;
   P.bmax = o.heavy_cutoff;
-  P.cap = 2 * kU * o.block;
+  P.cap = stage_capacity(o.block);
   int l = 0;
   while ((kFine << l) < (uint32_t)o.heavy_cutoff) l++;
   P.log2_bmax_fine = l;
@@ -387,6 +387,10 @@ gbf_status launch_bfs(Graph &g, Workspace &ws, int32_t src, int32_t *dist, int32
   P.inject_wait = o.inject_wait;
   P.cap_ns = o.spin_cap_ns;
   const size_t smem = push_smem_bytes(SmemShape{P.bmax, P.cap, 0, 0});
+  {
+    const gbf_status sm = check_smem(smem, "bfs_kernel");
+    if (sm != GBF_OK) return sm;
+  }
   GBF_CUDA(cudaFuncSetAttribute(bfs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem));
   int per_sm = 0;
@@ -409,7 +413,7 @@ gbf_status launch_bfs(Graph &g, Workspace &ws, int32_t src, int32_t *dist, int32
 }
 
 int resident_ctas_per_sm_bfs(const Opts &o) {
-  const size_t smem = push_smem_bytes(SmemShape{o.heavy_cutoff, 2 * kU * o.block, 0, 0});
+  const size_t smem = push_smem_bytes(SmemShape{o.heavy_cutoff, stage_capacity(o.block), 0, 0});
   if (cudaFuncSetAttribute(bfs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return 0;

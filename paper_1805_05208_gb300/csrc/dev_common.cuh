@@ -196,9 +196,18 @@ struct PushSmem {
   uint32_t cap_out;
 };
 
+// Staging capacity for a CTA of `block` threads: room for two passes of kU
+// appends per thread, capped (entries beyond it spill to global memory), and
+// never below two appends per thread (the conversion and update loops add up
+// to one entry per thread between flush checks).
+__host__ __device__ inline int stage_capacity(int block) {
+  const int c = 2 * kU * block;
+  return c < 8192 ? c : (8192 > 2 * block ? 8192 : 2 * block);
+}
+
 struct SmemShape {
   int bmax;   // largest chunk of the blocked edgeMap
-  int cap;    // staging capacity (>= 2 * kU * blockDim)
+  int cap;    // staging capacity (stage_capacity(blockDim))
   int filed;  // 1: reserve the bucket-filing stage
   int nB;     // bucket slots (histogram size)
 };

@@ -132,6 +132,10 @@ struct Opts {
 };
 Opts resolve(const gbf_options *o, const Graph &g, int kind);  // kind: GBF_TUNE_*
 
+// GBF_ERR_INVALID (with a message) if a CTA cannot get `bytes` of dynamic
+// shared memory on the current device.
+gbf_status check_smem(size_t bytes, const char *kernel);
+
 // Workspace management (graph.cu)
 gbf_status ws_ensure_base(Graph &g, Workspace &ws);
 gbf_status ws_ensure_wbfs(Graph &g, Workspace &ws, int nB);

@@ -27,6 +27,18 @@ gbf_status cuda_fail(cudaError_t e, const char *what) {
   return GBF_ERR_CUDA;
 }
 
+gbf_status check_smem(size_t bytes, const char *kernel) {
+  int dev = 0, optin = 0;
+  GBF_CUDA(cudaGetDevice(&dev));
+  GBF_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (bytes > (size_t)optin) {
+    set_error(std::string(kernel) + ": block size / heavy_cutoff need " + std::to_string(bytes) +
+              " bytes of shared memory per CTA, more than the device's " + std::to_string(optin));
+    return GBF_ERR_INVALID;
+  }
+  return GBF_OK;
+}
+
 // ------------------------------------------------------------------ options
 Opts resolve(const gbf_options *o, const Graph &g, int kind) {
   (void)g;

@@ -382,11 +382,15 @@ gbf_status launch_msbfs_rows(Graph &g, Workspace &ws, const int32_t *srcs_host, 
     P.pull_divisor = o.pull_divisor;
     P.pull_serial = o.pull_serial;
     P.bmax = o.heavy_cutoff;
-    P.cap = 2 * kU * o.block;
+    P.cap = stage_capacity(o.block);
     P.inject_wait = o.inject_wait;
     P.cap_ns = o.spin_cap_ns;
     const size_t smem = push_smem_bytes(SmemShape{P.bmax, P.cap, 0, 0});
-    GBF_CUDA(cudaFuncSetAttribute(msbfs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    {
+    const gbf_status sm = check_smem(smem, "msbfs_kernel");
+    if (sm != GBF_OK) return sm;
+  }
+  GBF_CUDA(cudaFuncSetAttribute(msbfs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
     int per_sm = 0;
     GBF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, msbfs_kernel, o.block, smem));
@@ -440,7 +444,7 @@ gbf_status launch_msbfs(Graph &g, Workspace &ws, const int32_t *srcs_host, int32
 }
 
 int resident_ctas_per_sm_msbfs(const Opts &o) {
-  const size_t smem = push_smem_bytes(SmemShape{o.heavy_cutoff, 2 * kU * o.block, 0, 0});
+  const size_t smem = push_smem_bytes(SmemShape{o.heavy_cutoff, stage_capacity(o.block), 0, 0});
   if (cudaFuncSetAttribute(msbfs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return 0;

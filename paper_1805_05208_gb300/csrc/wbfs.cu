@@ -510,7 +510,7 @@ gbf_status launch_wbfs(Graph &g, Workspace &ws, int32_t src, int32_t *dist, cons
   P.pull_divisor = o.pull_divisor;
   P.dense = o.dense_wbfs;
   P.bmax = o.heavy_cutoff;
-  P.cap = 2 * kU * o.block;
+  P.cap = stage_capacity(o.block);
   int l = 0;
   while ((kFine << l) < (uint32_t)o.heavy_cutoff) l++;
   P.log2_bmax_fine = l;
@@ -520,6 +520,10 @@ gbf_status launch_wbfs(Graph &g, Workspace &ws, int32_t src, int32_t *dist, cons
   P.cap_ns = o.spin_cap_ns;
   const size_t smem =
       push_smem_bytes(SmemShape{P.bmax, P.cap, 1, ws.nB}) + sizeof(uint32_t) * (size_t)ws.nB;
+  {
+    const gbf_status sm = check_smem(smem, "wbfs_kernel");
+    if (sm != GBF_OK) return sm;
+  }
   GBF_CUDA(cudaFuncSetAttribute(wbfs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem));
   int per_sm = 0;
@@ -542,7 +546,7 @@ gbf_status launch_wbfs(Graph &g, Workspace &ws, int32_t src, int32_t *dist, cons
 }
 
 int resident_ctas_per_sm_wbfs(const Opts &o, int nB) {
-  const size_t smem = push_smem_bytes(SmemShape{o.heavy_cutoff, 2 * kU * o.block, 1, nB}) +
+  const size_t smem = push_smem_bytes(SmemShape{o.heavy_cutoff, stage_capacity(o.block), 1, nB}) +
                       sizeof(uint32_t) * (size_t)nB;
   if (cudaFuncSetAttribute(wbfs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
