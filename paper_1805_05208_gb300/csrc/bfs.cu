@@ -295,6 +295,7 @@ __global__ void __launch_bounds__(1024) bfs_kernel(BfsParams P) {
   bool ok = grid_sync(ctl, bar, &s_flag);
 
   int fmt_bitmap = 0, qb = 0, fb = 0;
+  int bem = 0;  // blocked edgeMap invocations so far
   int level = 1;
   unsigned long long fr = ok ? ld_vol(ctl->fr[0]) : 0ull;
   while (ok) {
@@ -333,7 +334,7 @@ __global__ void __launch_bounds__(1024) bfs_kernel(BfsParams P) {
                       ctl};
       // every queued vertex has degree >= 2
       const int s = chunk_shift(D, (uint32_t)P.bmax, 2u);
-      blocked_edge_map(g, in, s, (uint32_t)P.bmax, S, fn, sink, ctl);
+      blocked_edge_map(g, in, s, (uint32_t)P.bmax, S, fn, sink, ctl, bem++);
       sink.finish(S);
       reached += fn.reached;
       qb ^= 1;

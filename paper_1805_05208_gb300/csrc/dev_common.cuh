@@ -191,7 +191,8 @@ struct PushSmem {
   int32_t *fs;
   uint32_t *hist;
   uint32_t *gbase;
-  uint32_t *misc;  // [0] n_out [1] pos [2] dpos [3] flag [4] n_filed [5] n_ovf [6] ovf pos [7] ovf min, [8..41] scan tmp
+  uint32_t *misc;  // [0] n_out [1] pos [2] dpos [3] flag [4] n_filed [5] n_ovf [6] ovf pos [7] ovf min,
+                   // [8..41] scan tmp, [48..49] next chunk of the blocked edgeMap
   unsigned long long *misc64;  // 32 entries
   uint32_t cap_out;
 };
@@ -414,34 +415,46 @@ __device__ __forceinline__ void walk_chunk(PushSmem &S, uint32_t m, uint32_t nv,
 // Blocked sparse edgeMap over the frontier `in` with chunks of B = 256 << s
 // edges located through the chunk-start table (edgeMapBlocked, Alg. 2).  A
 // chunk may span at most bmax + 1 frontier vertices (the shared arrays);
-// callers bound s by the smallest degree in the queue.
+// callers bound s by the smallest degree in the queue.  Each CTA starts with
+// chunk blockIdx.x and then takes chunks from a global counter, so CTAs that
+// finish early take up the slack of slow ones before the round's barrier.
+// `inv` numbers the calls of a launch (identically in every CTA): call inv
+// uses counter ctl->work[inv % 4] and clears ctl->work[(inv + 2) % 4], whose
+// last user finished before at least one grid barrier.
 template <class Fn, class Sink>
 __device__ __forceinline__ void blocked_edge_map(const DevGraph &g, const QueueIn &in, int s,
                                                  uint32_t bmax, PushSmem &S, Fn &fn, Sink &sink,
-                                                 Ctl *ctl) {
+                                                 Ctl *ctl, int inv) {
   const uint32_t B = kFine << s;
   const uint32_t nfine = (in.D + kFine - 1) >> kFineLog;
   const uint32_t nch = (in.D + B - 1) / B;
-  for (uint32_t c = blockIdx.x; c < nch; c += gridDim.x) {
+  unsigned int *work = &ctl->work[inv & 3];
+  if (blockIdx.x == 0 && threadIdx.x == 0) st_vol(ctl->work[(inv + 2) & 3], 0u);
+  uint32_t c = blockIdx.x;
+  for (uint32_t it = 0; c < nch; it++) {
     const uint32_t e_lo = c * B, e_hi = min(e_lo + B, in.D);
     const uint32_t f1 = (c + 1) << s;
     const uint32_t i0 = in.cs[c << s];
     const uint32_t i1 = (f1 < nfine) ? in.cs[f1] : in.cnt - 1;
-    if (i1 < i0 || i1 >= in.cnt || i1 - i0 > bmax) {  // inconsistent table: never expected
-      if (threadIdx.x == 0) raise_error(ctl, GBF_ERR_OVERFLOW, 3);
-      continue;
-    }
-    const uint32_t nv = i1 - i0 + 1;
+    const bool bad = i1 < i0 || i1 >= in.cnt || i1 - i0 > bmax;  // never expected
+    if (bad && threadIdx.x == 0) raise_error(ctl, GBF_ERR_OVERFLOW, 3);
+    const uint32_t nv = bad ? 0u : i1 - i0 + 1;
     for (uint32_t j = threadIdx.x; j < nv; j += blockDim.x) {
       int32_t u = in.q[i0 + j];
       S.base[j] = in.qoff[i0 + j];
       S.u[j] = u;
       S.adj[j] = __ldg(g.off + u);
     }
-    if (threadIdx.x == 0) S.base[nv] = (i1 + 1 < in.cnt) ? in.qoff[i1 + 1] : in.D;
+    if (threadIdx.x == 0 && nv) S.base[nv] = (i1 + 1 < in.cnt) ? in.qoff[i1 + 1] : in.D;
+    // The next chunk for this CTA, taken while the current one is walked.
+    // Two slots: a thread may still be reading the previous iteration's
+    // slot when thread 0 writes this one (at most one iteration apart, as
+    // every iteration holds a __syncthreads).
+    if (threadIdx.x == 0) S.misc[48 + (it & 1)] = gridDim.x + atomicAdd(work, 1u);
     __syncthreads();
-    walk_chunk(S, g.m, nv, e_lo, e_hi, fn, sink);
-    sink.chunk_end(S);
+    if (nv) walk_chunk(S, g.m, nv, e_lo, e_hi, fn, sink);
+    sink.chunk_end(S);  // starts with __syncthreads
+    c = S.misc[48 + (it & 1)];
   }
 }
 

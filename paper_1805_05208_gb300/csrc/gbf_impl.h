@@ -38,6 +38,7 @@ struct Ctl {
   unsigned int ovf_cnt[2];     // overflow bucket counts
   int ovf_min[2];              // overflow bucket minimum value
   unsigned int imask[3][32];   // buckets filed into during round t, by t % 3 (one bit per slot)
+  unsigned int work[4];        // dynamic chunk counters of the blocked edgeMap, by invocation % 4
   // statistics
   unsigned long long edges_scanned;
   unsigned long long expanded;

@@ -184,6 +184,7 @@ __global__ void __launch_bounds__(1024) msbfs_kernel(MsParams P) {
   ok = ok && grid_sync(ctl, bar, &s_flag);
 
   unsigned long long fr = ok ? ld_vol(ctl->fr[0]) : 0ull;
+  int bem = 0;  // blocked edgeMap invocations so far
   for (int32_t L = 1; ok; L++) {
     const uint32_t cnt = (uint32_t)(fr >> 32), D = (uint32_t)fr;
     if (cnt == 0) break;
@@ -213,7 +214,7 @@ __global__ void __launch_bounds__(1024) msbfs_kernel(MsParams P) {
       MsPushFn fn{g.tgt, cur, P.seen, P.next, 0};
       TouchSink sink{P.touched, tcount, n, ctl};
       blocked_edge_map(g, in, chunk_shift(D, (uint32_t)P.bmax, 1u), (uint32_t)P.bmax, S, fn, sink,
-                       ctl);
+                       ctl, bem++);
       if (blockIdx.x == 0 && threadIdx.x == 0) {
         scanned += D;
         expanded += cnt;

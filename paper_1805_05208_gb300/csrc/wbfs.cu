@@ -200,8 +200,10 @@ struct RelaxFn {
       v[r] = val[r] ? __ldg(tgt + idx[r]) : 0;
       nd[r] = val[r] ? b + (int32_t)__ldg(w + idx[r]) : kInf;
     }
+    // read D at L2 (.cg): L1 lines of D go stale as other SMs lower it, and a
+    // stale (larger) value only costs a writeMin that cannot succeed
 #pragma unroll
-    for (int r = 0; r < kU; r++) dv[r] = val[r] ? dist[v[r]] : kInf;
+    for (int r = 0; r < kU; r++) dv[r] = val[r] ? __ldcg(dist + v[r]) : kInf;
     bool low[kU];
 #pragma unroll
     for (int r = 0; r < kU; r++) {
@@ -335,6 +337,7 @@ __global__ void __launch_bounds__(1024) wbfs_kernel(WbfsParams P) {
   bool ok = grid_sync(ctl, bar, &s_flag);
 
   int32_t lo = 0;
+  int bem = 0;         // blocked edgeMap invocations so far
   int cur = 0;         // active overflow buffer
   int32_t prev = -1;   // slot consumed by the previous round (-1: none)
   for (int32_t t = 1; ok; t++) {
@@ -463,7 +466,7 @@ __global__ void __launch_bounds__(1024) wbfs_kernel(WbfsParams P) {
       QueueIn in{P.q, P.qoff, P.cs, hcnt, hD};
       // every heavy vertex has more than P.heavy edges
       blocked_edge_map(g, in, chunk_shift(hD, (uint32_t)P.bmax, (uint32_t)P.heavy + 1u),
-                       (uint32_t)P.bmax, S, fn, fsink, ctl);
+                       (uint32_t)P.bmax, S, fn, fsink, ctl, bem++);
       fsink.flush(S);
       if (blockIdx.x == 0 && threadIdx.x == 0) c.scanned += hD;
       if (!grid_sync(ctl, bar, &s_flag)) break;
