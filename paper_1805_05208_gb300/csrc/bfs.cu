@@ -17,6 +17,8 @@
 // graph all its neighbours are already visited.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "dev_common.cuh"
 #include "gbf_impl.h"
 
@@ -29,7 +31,7 @@ struct BfsParams {
   int32_t *dist;
   int32_t *parent;
   uint32_t *visited;
-  uint32_t *fbm[2];
+  uint32_t *fbm[3];  // frontier bitmaps: input, output, cleared for the next level
   int32_t *q[2];
   uint32_t *qoff[2];
   uint32_t *cs[2];
@@ -94,136 +96,296 @@ struct BfsPushFn {
   }
 };
 
-// Dense direction: one warp per 32-vertex word of the bitmaps.  Each
-// unvisited vertex checks its first arcs (4 at a time, loads batched); the
-// warp then walks the remaining arcs of every still-unresolved vertex of the
-// word together, 32 consecutive arcs per window and kU windows per step,
-// dropping a vertex as soon as one of its arcs hits the frontier.  Arcs are
-// taken in CSR order and the first hit becomes the parent, as in a
-// sequential early-exit scan.
-__device__ void pull_level(const BfsParams &P, const uint32_t *fin, uint32_t *fout, int32_t level,
-                           unsigned long long *counter, unsigned long long &scanned,
-                           unsigned long long &reached, unsigned long long &cand_cnt,
-                           unsigned long long *s64) {
-  const DevGraph &g = P.g;
-  const int lane = threadIdx.x & 31;
-  const uint32_t nwords = ((uint32_t)g.n + 31) >> 5;
-  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t tw = (gridDim.x * blockDim.x) >> 5;
-  const uint32_t first = (uint32_t)P.pull_serial;
-  uint32_t my_cnt = 0, my_deg = 0;
-  for (uint32_t wi = gw; wi < nwords; wi += tw) {
-    const uint32_t vis = P.visited[wi];
-    const int32_t v = (int32_t)(wi * 32 + lane);
-    bool cand = v < g.n && !((vis >> lane) & 1u);
-    uint32_t s = 0, e = 0;
-    if (cand) {
-      s = __ldg(g.off + v);
-      e = __ldg(g.off + v + 1);
-      cand = e > s;
-      cand_cnt++;
-    }
-    int32_t par = -1;
-    // pass 1: the first arcs of each candidate, four loads in flight per lane
-    uint32_t k = s;
-    for (uint32_t c = 0; c < first; c += 4) {
-      int32_t u[4];
-      bool h[4];
-#pragma unroll
-      for (int r = 0; r < 4; r++) {
-        const uint32_t kk = k + r;
-        u[r] = (cand && par < 0 && kk < e) ? __ldg(g.tgt + kk) : -1;
-      }
-#pragma unroll
-      for (int r = 0; r < 4; r++) h[r] = u[r] >= 0 && ((fin[u[r] >> 5] >> (u[r] & 31)) & 1u);
-      if (cand && par < 0) {
-        uint32_t used = min(4u, e - min(k, e));
-#pragma unroll
-        for (int r = 3; r >= 0; r--)
-          if (h[r]) {
-            par = u[r];
-            used = (uint32_t)r + 1;
-          }
-        scanned += used;
-        k += used;
-      }
-    }
-    // pass 2: the remaining arcs of the unresolved candidates, warp windows
-    const uint32_t rem = (cand && par < 0 && k < e) ? e - k : 0u;
-    uint32_t incl = rem;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(kFull, incl, o);
-      if (lane >= o) incl += y;
-    }
-    const uint32_t total = __shfl_sync(kFull, incl, 31);
-    const uint32_t excl = incl - rem;
-    unsigned pending = __ballot_sync(kFull, rem > 0);
-    for (uint32_t w0 = 0; w0 < total && pending; w0 += 32 * kU) {
-      int32_t uu[kU];
-      int own[kU];
-      bool hit[kU];
-#pragma unroll
-      for (int r = 0; r < kU; r++) {
-        const uint32_t ee = w0 + 32 * r + lane;
-        int o = 0;
-#pragma unroll
-        for (int st = 16; st > 0; st >>= 1) {
-          const uint32_t cv = __shfl_sync(kFull, incl, o + st - 1);
-          if (cv <= ee) o += st;
-        }
-        o = min(o, 31);
-        const uint32_t eo = __shfl_sync(kFull, excl, o);
-        const uint32_t ko = __shfl_sync(kFull, k, o);
-        const bool val = ee < total && ((pending >> o) & 1u);
-        own[r] = o;
-        uu[r] = val ? __ldg(g.tgt + ko + (ee - eo)) : -1;
-      }
-#pragma unroll
-      for (int r = 0; r < kU; r++) hit[r] = uu[r] >= 0 && ((fin[uu[r] >> 5] >> (uu[r] & 31)) & 1u);
-#pragma unroll
-      for (int r = 0; r < kU; r++) {
-        const unsigned lb = __ballot_sync(kFull, uu[r] >= 0);
-        if (lane == 0) scanned += __popc(lb);
-        unsigned hb = __ballot_sync(kFull, hit[r]);
-        while (hb) {
-          const int f = __ffs(hb) - 1;
-          const int o = __shfl_sync(kFull, own[r], f);
-          const int32_t uf = __shfl_sync(kFull, uu[r], f);
-          if (lane == o && par < 0) par = uf;
-          hb &= ~__ballot_sync(kFull, hit[r] && own[r] == o);
-          pending &= ~(1u << o);
-        }
-      }
-    }
-    const bool got = par >= 0;
-    const unsigned nb = __ballot_sync(kFull, got);
-    if (got) {
-      P.dist[v] = level;
-      if (P.parent) P.parent[v] = par;
-      reached++;
-      const uint32_t d = e - s;
-      if (d >= 2) {
-        my_cnt++;
-        my_deg += d;
-      }
-    }
-    if (lane == 0) {
-      fout[wi] = nb;
-      if (nb) P.visited[wi] = vis | nb;
+// Dense direction (the early-exit pull of §3) as one stream of candidates per
+// warp.  Warps take chunks of kChunkWords bitmap words from a global counter;
+// a word group (kGroupWords words: visited word and the offsets of every
+// vertex) is loaded one step before it is needed and its candidates
+// (unvisited, degree > 0) are appended to the warp's ring in shared memory.
+// Every step each lane checks the next 4 arcs of its candidate in CSR order
+// and takes a new candidate from the ring as soon as its own resolves, so no
+// lane waits for another except at the end of the level.  A candidate still
+// unresolved after `pull_serial` arcs is parked in the lane (a lane whose
+// slot is taken keeps scanning its candidate itself); once kWalkLanes lanes
+// hold one, the warp walks the remaining arcs of all parked candidates
+// together (pull_walk_parked), 128 arcs per step.  Words are owned by one warp, whose
+// found vertices set their next-frontier and visited bits with one atomicOr
+// per word and step.  The first frontier neighbour in CSR order becomes the
+// parent, as in a sequential early-exit scan.
+constexpr uint32_t kChunkWords = 32;
+constexpr uint32_t kGroupWords = 4;
+constexpr uint32_t kRing = 256;  // ring entries per warp: 8 per thread of the staging area
+constexpr int kWalkLanes = 16;   // parked candidates that start a warp walk
+
+// Per-thread counters of a pull level (32-bit: a thread's share of one level
+// fits), and the write of a found vertex's distance and parent.
+struct PullCtx {
+  int32_t level;
+  uint32_t scanned, reached;
+  uint32_t cnt, deg;  // found vertices of degree >= 2 and their degree sum
+
+  __device__ __forceinline__ void record(const BfsParams &P, int32_t v, int32_t par, uint32_t d) {
+    P.dist[v] = level;
+    if (P.parent) P.parent[v] = par;
+    reached++;
+    if (d >= 2) {
+      cnt++;
+      deg += d;
     }
   }
-  unsigned long long packed = ((unsigned long long)my_cnt << 32) | my_deg;
-  unsigned long long tot = block_sum64(packed, s64);
+};
+
+// Warp-collective: walk the remaining arcs [k, e) of the lanes' parked
+// entries (v >= 0) in 32-arc windows, kU windows per step, in CSR order; a
+// vertex drops out at its first frontier neighbour.  Clears the parked slots.
+__device__ __forceinline__ void pull_walk_parked(const BfsParams &P, const uint32_t *fin,
+                                                 uint32_t *fout, PullCtx &C, int32_t &v,
+                                                 uint32_t k, uint32_t e, uint32_t s0) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t rem = v >= 0 ? e - k : 0u;
+  uint32_t incl = rem;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const uint32_t total = __shfl_sync(kFull, incl, 31);
+  const uint32_t excl = incl - rem;
+  unsigned pending = __ballot_sync(kFull, rem > 0);
+  int32_t par = -1;
+  for (uint32_t w0 = 0; w0 < total && pending; w0 += 32 * kU) {
+    int32_t uu[kU];
+    int own[kU];
+    bool hit[kU];
+#pragma unroll
+    for (int r = 0; r < kU; r++) {
+      const uint32_t ee = w0 + 32 * r + lane;
+      int o = 0;
+#pragma unroll
+      for (int st = 16; st > 0; st >>= 1) {
+        const uint32_t cv = __shfl_sync(kFull, incl, o + st - 1);
+        if (cv <= ee) o += st;
+      }
+      o = min(o, 31);
+      const uint32_t eo = __shfl_sync(kFull, excl, o);
+      const uint32_t ko = __shfl_sync(kFull, k, o);
+      const bool val = ee < total && ((pending >> o) & 1u);
+      own[r] = o;
+      uu[r] = val ? __ldg(P.g.tgt + ko + (ee - eo)) : -1;
+    }
+#pragma unroll
+    for (int r = 0; r < kU; r++)
+      hit[r] = uu[r] >= 0 && ((fin[uu[r] >> 5] >> (uu[r] & 31)) & 1u);
+#pragma unroll
+    for (int r = 0; r < kU; r++) {
+      const unsigned lb = __ballot_sync(kFull, uu[r] >= 0);
+      if (lane == 0) C.scanned += __popc(lb);
+      unsigned hb = __ballot_sync(kFull, hit[r]);
+      while (hb) {
+        const int f = __ffs(hb) - 1;
+        const int o = __shfl_sync(kFull, own[r], f);
+        const int32_t uf = __shfl_sync(kFull, uu[r], f);
+        if (lane == o && par < 0) par = uf;
+        hb &= ~__ballot_sync(kFull, hit[r] && own[r] == o);
+        pending &= ~(1u << o);
+      }
+    }
+  }
+  if (par >= 0) {
+    C.record(P, v, par, e - s0);
+    const uint32_t w = (uint32_t)v >> 5, bit = 1u << (v & 31);
+    atomicOr(fout + w, bit);
+    atomicOr(P.visited + w, bit);
+  }
+  v = -1;
+}
+
+__device__ void pull_level(const BfsParams &P, PushSmem &S, const uint32_t *fin, uint32_t *fout,
+                           uint32_t *fzero, int32_t level, unsigned long long *counter,
+                           unsigned long long &scanned, unsigned long long &reached,
+                           unsigned long long &cand_cnt, int inv) {
+  const DevGraph &g = P.g;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const uint32_t nwords = ((uint32_t)g.n + 31) >> 5;
+  const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  // the bitmap the next dense level writes (nobody reads it in this level)
+  for (uint32_t i = gt; i < nwords; i += gs) fzero[i] = 0u;
+  const uint32_t nchunk = (nwords + kChunkWords - 1) / kChunkWords;
+  const uint32_t F = (uint32_t)P.pull_serial;
+  const unsigned lt = (1u << lane) - 1u;
+  int32_t *rv = S.out_v + warp * kRing;
+  uint32_t *rs = S.out_d + warp * kRing, *re = S.pref + warp * kRing;
+  uint32_t *scr = S.base + warp * 32;  // per-word bit gathering of one step
+  scr[lane] = 0u;
+  __syncwarp();
+  PullCtx C{level, 0u, 0u, 0u, 0u};
+  unsigned int *work = &P.ctl->work[inv & 3];
+  if (blockIdx.x == 0 && threadIdx.x == 0) st_vol(P.ctl->work[(inv + 2) & 3], 0u);
+  const uint32_t twarps = gridDim.x * (uint32_t)nw;
+
+  // word supply: chunk = first chunk of this warp, then from the counter (the
+  // next one is requested by lane 0 one chunk ahead)
+  uint32_t chunk = blockIdx.x * (uint32_t)nw + (uint32_t)warp;
+  uint32_t next_chunk = 0;
+  if (lane == 0) next_chunk = twarps + atomicAdd(work, 1u);
+  uint32_t gw = chunk * kChunkWords;  // first word of the next group to load
+  bool more = chunk < nchunk;
+  bool have = false;
+  uint32_t pw = 0;
+  // the loaded group: offsets of its vertices (pa[r]: word r; the end offset of
+  // a lane's vertex is the next lane's start, pnext after the last word) and
+  // its visited words (lane r holds word r)
+  uint32_t pa[kGroupWords], pnext = 0, pvis = ~0u;
+  uint32_t head = 0, tail = 0;
+  int32_t cv = -1, pv = -1;
+  uint32_t ck = 0, ce = 0, cs0 = 0, pk = 0, pe = 0, ps0 = 0;
+
+  // load the next word group (warp-uniform)
+#define GBF_PULL_PREFETCH()                                                              \
+  do {                                                                                   \
+    _Pragma("unroll") for (uint32_t r = 0; r < kGroupWords; r++) {                       \
+      const uint32_t v = (gw + r) * 32 + lane;                                           \
+      pa[r] = v <= (uint32_t)g.n ? __ldg(g.off + v) : 0u;                                \
+    }                                                                                    \
+    {                                                                                    \
+      const uint32_t vn = (gw + kGroupWords) * 32;                                       \
+      pnext = (lane == 31 && vn <= (uint32_t)g.n) ? __ldg(g.off + vn) : 0u;              \
+      pvis = ((uint32_t)lane < kGroupWords && gw + lane < nwords) ? P.visited[gw + lane]  \
+                                                                  : ~0u;                 \
+    }                                                                                    \
+    pw = gw;                                                                             \
+    have = true;                                                                         \
+    gw += kGroupWords;                                                                   \
+    if (gw >= min(chunk * kChunkWords + kChunkWords, nwords)) {                          \
+      chunk = __shfl_sync(kFull, next_chunk, 0);                                         \
+      more = chunk < nchunk;                                                             \
+      if (more) {                                                                        \
+        gw = chunk * kChunkWords;                                                        \
+        if (lane == 0) next_chunk = twarps + atomicAdd(work, 1u);                        \
+      }                                                                                  \
+    }                                                                                    \
+  } while (0)
+
+  if (more) GBF_PULL_PREFETCH();
+  while (true) {
+    // append the loaded group's candidates, then start loading the next group
+    if (have && tail - head < kRing - 32 * kGroupWords - 32) {
+#pragma unroll
+      for (uint32_t r = 0; r < kGroupWords; r++) {
+        const uint32_t vis = __shfl_sync(kFull, pvis, r);
+        const uint32_t a = pa[r];
+        uint32_t z = __shfl_down_sync(kFull, a, 1);
+        const uint32_t zn = (r + 1 < kGroupWords) ? __shfl_sync(kFull, pa[r + 1 < kGroupWords ? r + 1 : r], 0)
+                                                  : pnext;
+        if (lane == 31) z = zn;
+        const uint32_t v = (pw + r) * 32 + lane;
+        const bool c = v < (uint32_t)g.n && !((vis >> lane) & 1u) && z > a;
+        const unsigned bal = __ballot_sync(kFull, c);
+        if (c) {
+          const uint32_t i = (tail + __popc(bal & lt)) & (kRing - 1);
+          rv[i] = (int32_t)v;
+          rs[i] = a;
+          re[i] = z;
+        }
+        tail += __popc(bal);
+      }
+      have = false;
+      __syncwarp();
+      if (more) GBF_PULL_PREFETCH();
+    }
+    // lanes without a candidate take the next ones from the ring
+    const unsigned need = __ballot_sync(kFull, cv < 0);
+    const uint32_t avail = tail - head;
+    if (cv < 0) {
+      const uint32_t r = __popc(need & lt);
+      if (r < avail) {
+        const uint32_t i = (head + r) & (kRing - 1);
+        cv = rv[i];
+        ck = cs0 = rs[i];
+        ce = re[i];
+        cand_cnt++;
+      }
+    }
+    head += min((uint32_t)__popc(need), avail);
+    const bool act = cv >= 0;
+    if (!__any_sync(kFull, act)) {
+      if (!have) break;
+      continue;
+    }
+    // one step: the next 4 arcs of each lane's candidate
+    int32_t u[4];
+#pragma unroll
+    for (int r = 0; r < 4; r++) u[r] = (act && ck + r < ce) ? __ldg(g.tgt + ck + r) : -1;
+    bool h[4];
+#pragma unroll
+    for (int r = 0; r < 4; r++) h[r] = u[r] >= 0 && ((fin[u[r] >> 5] >> (u[r] & 31)) & 1u);
+    bool park = false, got = false;
+    int32_t gv = 0;
+    if (act) {
+      uint32_t used = min(4u, ce - ck);
+      int32_t par = -1;
+#pragma unroll
+      for (int r = 3; r >= 0; r--)
+        if (h[r]) {
+          par = u[r];
+          used = (uint32_t)r + 1;
+        }
+      C.scanned += used;
+      ck += used;
+      if (par >= 0) {
+        C.record(P, cv, par, ce - cs0);
+        got = true;
+        gv = cv;
+        cv = -1;
+      } else if (ck >= ce) {
+        cv = -1;
+      } else {
+        park = pv < 0 && ck - cs0 >= F;
+      }
+    }
+    // one atomicOr per distinct word of this step's found vertices
+    if (__any_sync(kFull, got)) {
+      const uint32_t key = got ? ((uint32_t)gv >> 5) : (0xF0000000u | (uint32_t)lane);
+      const unsigned grp = __match_any_sync(kFull, key);
+      const int leader = __ffs(grp) - 1;
+      if (got) atomicOr(scr + leader, 1u << (gv & 31));
+      __syncwarp();
+      if (got && lane == leader) {
+        const uint32_t bits = scr[lane];
+        scr[lane] = 0u;
+        atomicOr(fout + key, bits);
+        atomicOr(P.visited + key, bits);
+      }
+      __syncwarp();
+    }
+    if (park) {
+      pv = cv;
+      pk = ck;
+      pe = ce;
+      ps0 = cs0;
+      cv = -1;
+    }
+    if (__popc(__ballot_sync(kFull, pv >= 0)) >= kWalkLanes)
+      pull_walk_parked(P, fin, fout, C, pv, pk, pe, ps0);
+  }
+#undef GBF_PULL_PREFETCH
+  if (__any_sync(kFull, pv >= 0)) pull_walk_parked(P, fin, fout, C, pv, pk, pe, ps0);
+  scanned += C.scanned;
+  reached += C.reached;
+  unsigned long long packed = ((unsigned long long)C.cnt << 32) | C.deg;
+  unsigned long long tot = block_sum64(packed, S.misc64);
   if (threadIdx.x == 0 && tot) atomicAdd(counter, tot);
 }
 
-// Sparse queue -> bitmap (cleared first; two barriers).
+// Sparse queue -> bitmap fb (cleared first, with the bitmap fo the next
+// dense level writes; two barriers).
 __device__ bool queue_to_bitmap(const BfsParams &P, const int32_t *q, uint32_t cnt, uint32_t *fb,
-                                Barrier &bar, int *s_flag) {
+                                uint32_t *fo, Barrier &bar, int *s_flag) {
   const uint32_t nwords = ((uint32_t)P.g.n + 31) >> 5;
   const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
-  for (uint32_t i = gt; i < nwords; i += gs) fb[i] = 0u;
+  for (uint32_t i = gt; i < nwords; i += gs) {
+    fb[i] = 0u;
+    fo[i] = 0u;
+  }
   if (!grid_sync(P.ctl, bar, s_flag)) return false;
   for (uint32_t i = gt; i < cnt; i += gs) {
     const int32_t v = q[i];
@@ -233,25 +395,36 @@ __device__ bool queue_to_bitmap(const BfsParams &P, const int32_t *q, uint32_t c
 }
 
 // Bitmap -> sparse queue with degree prefix (CTA-contiguous word ranges).
+// Each warp takes 2 kU words per step with all their loads in flight; the
+// staging area holds one step of the whole CTA (2 kU entries per thread, the
+// staging capacity), so it is flushed between steps whenever it is not empty.
 __device__ void bitmap_to_queue(const BfsParams &P, const uint32_t *fb, PushSmem &S,
                                 const QueueOut &out) {
+  constexpr int R = 2 * kU;
   const uint32_t nwords = ((uint32_t)P.g.n + 31) >> 5;
   const uint32_t per = (nwords + gridDim.x - 1) / gridDim.x;
   const uint32_t wlo = min(nwords, blockIdx.x * per), whi = min(nwords, wlo + per);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (uint32_t base = wlo; base < whi; base += nw) {
-    const uint32_t wi = base + warp;
-    const uint32_t bits = (wi < whi) ? fb[wi] : 0u;
-    bool emit = false;
-    int32_t v = (int32_t)(wi * 32 + lane);
-    uint32_t d = 0;
-    if ((bits >> lane) & 1u) {
-      d = __ldg(P.g.off + v + 1) - __ldg(P.g.off + v);
-      emit = d >= 2;
+  for (uint32_t base = wlo; base < whi; base += R * nw) {
+    uint32_t a[R], z[R];
+    bool set[R];
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      const uint32_t wi = base + warp + r * nw;
+      const uint32_t bits = (wi < whi) ? fb[wi] : 0u;
+      set[r] = (bits >> lane) & 1u;
+      const int32_t v = (int32_t)(wi * 32 + lane);
+      a[r] = set[r] ? __ldg(P.g.off + v) : 0u;
+      z[r] = set[r] ? __ldg(P.g.off + v + 1) : 0u;
     }
-    stage_append(S, emit, v, d);
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+      const uint32_t wi = base + warp + r * nw;
+      const uint32_t d = z[r] - a[r];
+      stage_append(S, set[r] && d >= 2, (int32_t)(wi * 32 + lane), d);
+    }
     __syncthreads();
-    if (S.misc[0] + blockDim.x > S.cap_out) stage_flush(S, out, P.ctl);
+    stage_make_room(S, out, P.ctl, R * blockDim.x);
   }
   stage_flush(S, out, P.ctl);
 }
@@ -304,7 +477,7 @@ __global__ void __launch_bounds__(1024) bfs_kernel(BfsParams P) {
     const bool dense =
         P.pull_divisor > 0 && (unsigned long long)D * (unsigned)P.pull_divisor > g.m;
     if (dense && !fmt_bitmap) {
-      if (!queue_to_bitmap(P, P.q[qb], cnt, P.fbm[0], bar, &s_flag)) break;
+      if (!queue_to_bitmap(P, P.q[qb], cnt, P.fbm[0], P.fbm[1], bar, &s_flag)) break;
       fmt_bitmap = 1;
       fb = 0;
     } else if (!dense && fmt_bitmap) {
@@ -339,9 +512,9 @@ __global__ void __launch_bounds__(1024) bfs_kernel(BfsParams P) {
       reached += fn.reached;
       qb ^= 1;
     } else {
-      pull_level(P, P.fbm[fb], P.fbm[fb ^ 1], level, outc, scanned, reached, expanded,
-                 S.misc64);
-      fb ^= 1;
+      pull_level(P, S, P.fbm[fb], P.fbm[(fb + 1) % 3], P.fbm[(fb + 2) % 3], level, outc, scanned,
+                 reached, expanded, bem++);
+      fb = (fb + 1) % 3;
     }
     if (!grid_sync(ctl, bar, &s_flag)) break;
     fr = ld_vol(*outc);
@@ -368,8 +541,8 @@ gbf_status launch_bfs(Graph &g, Workspace &ws, int32_t src, int32_t *dist, int32
   P.dist = dist;
   P.parent = parent;
   P.visited = ws.visited;
+  for (int i = 0; i < 3; i++) P.fbm[i] = ws.fbm[i];
   for (int i = 0; i < 2; i++) {
-    P.fbm[i] = ws.fbm[i];
     P.q[i] = ws.q[i];
     P.qoff[i] = ws.qoff[i];
     P.cs[i] = ws.cs[i];

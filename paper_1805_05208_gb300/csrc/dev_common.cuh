@@ -337,6 +337,17 @@ __device__ __forceinline__ void stage_flush(PushSmem &S, const QueueOut &out, Ct
   __syncthreads();
 }
 
+// CTA-collective, called right after a __syncthreads that follows the last
+// appends: flush unless `room` more entries fit.  The barrier between the
+// read and the flush keeps every thread's read of the count ahead of any
+// thread's next append, so all threads take the same decision.
+__device__ __forceinline__ void stage_make_room(PushSmem &S, const QueueOut &out, Ctl *ctl,
+                                                uint32_t room) {
+  const bool full = S.misc[0] + room > S.cap_out;
+  __syncthreads();
+  if (full) stage_flush(S, out, ctl);
+}
+
 // Input frontier description.
 struct QueueIn {
   const int32_t *q;

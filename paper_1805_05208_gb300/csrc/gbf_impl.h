@@ -75,7 +75,7 @@ struct Workspace {
   uint32_t m = 0;
   size_t bytes = 0;
   uint32_t *visited = nullptr;   // ceil(n/32) words
-  uint32_t *fbm[2] = {nullptr, nullptr};
+  uint32_t *fbm[3] = {nullptr, nullptr, nullptr};
   int32_t *q[2] = {nullptr, nullptr};
   uint32_t *qoff[2] = {nullptr, nullptr};
   uint32_t *cs[2] = {nullptr, nullptr};  // chunk starts, one per 256 frontier edges

@@ -61,7 +61,10 @@ Opts resolve(const gbf_options *o, const Graph &g, int kind) {
   r.bucket_window = o->bucket_window;
   r.dense_wbfs = o->dense_wbfs ? 1 : 0;
   r.ctas = o->ctas > 0 ? o->ctas : 0;
-  r.pull_serial = o->pull_serial > 0 ? std::min(o->pull_serial, 1 << 20) : d.pull_serial;
+  // pull_serial 0: per-kind default (the BFS pull hands long scans to a warp
+  // walk only rarely; the multi-source pull after a few arcs)
+  r.pull_serial = o->pull_serial > 0 ? std::min(o->pull_serial, 1 << 20)
+                                     : (kind == GBF_TUNE_MSBFS ? 8 : 32);
   r.inject_wait = o->inject_wait ? 1 : 0;
   long long us = o->spin_cap_us > 0 ? o->spin_cap_us : d.spin_cap_us;
   r.spin_cap_ns = us * 1000LL;
@@ -187,6 +190,7 @@ gbf_status ws_ensure_base(Graph &g, Workspace &ws) {
   ws.n = g.n;
   ws.m = g.m;
   GBF_TRY(dmalloc(&ws.visited, nw, acc));
+  GBF_TRY(dmalloc(&ws.fbm[2], nw, acc));
   for (int i = 0; i < 2; i++) {
     GBF_TRY(dmalloc(&ws.fbm[i], nw, acc));
     GBF_TRY(dmalloc(&ws.q[i], n, acc));
@@ -272,7 +276,7 @@ gbf_status ws_ensure_msbfs(Graph &g, Workspace &ws, bool host_out) {
 }
 
 void ws_free(Workspace &ws) {
-  void *ptrs[] = {ws.visited, ws.fbm[0], ws.fbm[1], ws.q[0], ws.q[1], ws.qoff[0], ws.qoff[1],
+  void *ptrs[] = {ws.visited, ws.fbm[0], ws.fbm[1], ws.fbm[2], ws.q[0], ws.q[1], ws.qoff[0], ws.qoff[1],
                   ws.cs[0], ws.cs[1], ws.ctl, ws.dist_tmp, ws.parent_tmp, ws.trace, ws.slots,
                   ws.slot_cnt, ws.ovf[0], ws.ovf[1], ws.ms_seen, ws.ms_visit, ws.ms_next,
                   ws.ms_q[2], ws.ms_qoff[2], ws.ms_cs[2], ws.ms_touched, ws.ms_call,
@@ -334,7 +338,7 @@ gbf_status gbf_options_default(gbf_options *opt) {
   opt->dense_wbfs = 0;
   opt->spin_cap_us = 5000000;
   opt->ctas = 0;
-  opt->pull_serial = 8;
+  opt->pull_serial = 0;
   opt->inject_wait = 0;
   return GBF_OK;
 }

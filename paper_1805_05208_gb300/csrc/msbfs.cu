@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(1024) msbfs_kernel(MsParams P) {
         }
         stage_append(S, nwb != 0ull && d > 0, v, d);
         __syncthreads();
-        if (S.misc[0] + blockDim.x > S.cap_out) stage_flush(S, fout, ctl);
+        stage_make_room(S, fout, ctl, blockDim.x);
       }
       stage_flush(S, fout, ctl);
     } else {
@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(1024) msbfs_kernel(MsParams P) {
         write_rows(rows, k, v, inr ? nwb : 0ull, L);
         stage_append(S, nwb != 0ull && e > s, v, e - s);
         __syncthreads();
-        if (S.misc[0] + blockDim.x > S.cap_out) stage_flush(S, fout, ctl);
+        stage_make_room(S, fout, ctl, blockDim.x);
       }
       stage_flush(S, fout, ctl);
     }

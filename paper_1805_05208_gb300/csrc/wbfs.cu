@@ -450,8 +450,8 @@ __global__ void __launch_bounds__(1024) wbfs_kernel(WbfsParams P) {
       }
       __syncthreads();
       walk_chunk(S, g.m, nv, 0u, E, fn, fsink);
-      fsink.chunk_end(S);
-      if (S.misc[0] + blockDim.x > S.cap_out) stage_flush(S, fout, ctl);
+      fsink.chunk_end(S);  // starts with __syncthreads; leaves misc[0] alone
+      stage_make_room(S, fout, ctl, blockDim.x);
     }
     stage_flush(S, fout, ctl);
     fsink.flush(S);
