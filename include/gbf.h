@@ -332,7 +332,7 @@ gbf_status gbf_trace(gbf_graph *g, gbf_round_trace *out, int32_t cap, int32_t *c
  *   opt       NULL for defaults
  *   cuda_stream  stream to run on; the call blocks until the search is done
  *             and returns the device-side status
- * The call allocates nothing: its scratch (~18.2 MB) is one fixed array in
+ * The call allocates nothing: its scratch (~26.7 MB) is one fixed array in
  * the library's device module, held on every GPU that loads the library
  * until the process exits.  The first call on a device looks up that array's
  * device address (cudaGetSymbolAddress) with the device current; make that

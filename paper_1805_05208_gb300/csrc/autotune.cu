@@ -191,6 +191,10 @@ extern "C" gbf_status gbf_autotune(gbf_graph *h, int32_t kind, gbf_options *out)
             continue;
           float ms = 0;
           s = measure(c, &ms);
+          if (s == GBF_ERR_INVALID) {  // does not fit this device (shared memory): skip it
+            s = GBF_OK;
+            continue;
+          }
           if (s != GBF_OK) break;
           if (ms < best_ms * 0.97f) {
             best = c;

@@ -34,6 +34,7 @@ struct BfsParams {
   uint32_t *fbm[3];  // frontier bitmaps: input, output, cleared for the next level
   int32_t *q[2];
   uint32_t *qoff[2];
+  uint32_t *qadj[2];
   uint32_t *cs[2];
   uint32_t cs_cap;
   Ctl *ctl;
@@ -91,7 +92,7 @@ struct BfsPushFn {
 #pragma unroll
     for (int r = 0; r < kU; r++) {
       const uint32_t d = z[r] - a[r];
-      sink.append(S, win[r] && d >= 2, v[r], d);
+      sink.append(S, win[r] && d >= 2, v[r], d, a[r]);
     }
   }
 };
@@ -421,7 +422,7 @@ __device__ void bitmap_to_queue(const BfsParams &P, const uint32_t *fb, PushSmem
     for (int r = 0; r < R; r++) {
       const uint32_t wi = base + warp + r * nw;
       const uint32_t d = z[r] - a[r];
-      stage_append(S, set[r] && d >= 2, (int32_t)(wi * 32 + lane), d);
+      stage_append(S, set[r] && d >= 2, (int32_t)(wi * 32 + lane), d, a[r]);
     }
     __syncthreads();
     stage_make_room(S, out, P.ctl, R * blockDim.x);
@@ -434,7 +435,7 @@ __device__ void bitmap_to_queue(const BfsParams &P, const uint32_t *fb, PushSmem
 __global__ void __launch_bounds__(1024) bfs_kernel(BfsParams P) {
   extern __shared__ unsigned long long smem_raw[];
   __shared__ int s_flag;
-  PushSmem S = carve_push_smem(smem_raw, SmemShape{P.bmax, P.cap, 0, 0});
+  PushSmem S = carve_push_smem(smem_raw, SmemShape{P.bmax, P.cap, 0, 0, 1});
   if (threadIdx.x == 0) S.misc[0] = 0;
   Ctl *ctl = P.ctl;
   Barrier bar{0u, P.cap_ns};
@@ -457,6 +458,7 @@ __global__ void __launch_bounds__(1024) bfs_kernel(BfsParams P) {
     if (threadIdx.x == 0 && d0 > 0) {
       P.q[0][0] = src;
       P.qoff[0][0] = 0;
+      P.qadj[0][0] = __ldg(g.off + src);
       st_vol(ctl->fr[0], (1ull << 32) | d0);
     }
     for (uint32_t c = threadIdx.x; c < (d0 + kFine - 1) / kFine; c += blockDim.x)
@@ -481,7 +483,7 @@ __global__ void __launch_bounds__(1024) bfs_kernel(BfsParams P) {
       fmt_bitmap = 1;
       fb = 0;
     } else if (!dense && fmt_bitmap) {
-      QueueOut out{P.q[0], P.qoff[0], P.cs[0], &ctl->conv, (uint32_t)g.n, P.cs_cap};
+      QueueOut out{P.q[0], P.qoff[0], P.qadj[0], P.cs[0], &ctl->conv, (uint32_t)g.n, P.cs_cap};
       bitmap_to_queue(P, P.fbm[fb], S, out);
       if (!grid_sync(ctl, bar, &s_flag)) break;
       fmt_bitmap = 0;
@@ -500,13 +502,14 @@ __global__ void __launch_bounds__(1024) bfs_kernel(BfsParams P) {
       atomicAdd(&ctl->rounds, 1);
     }
     if (!fmt_bitmap) {
-      QueueIn in{P.q[qb], P.qoff[qb], P.cs[qb], cnt, D};
+      QueueIn in{P.q[qb], P.qoff[qb], P.qadj[qb], P.cs[qb], cnt, D};
       BfsPushFn fn{g.off, g.tgt, P.visited, P.dist, P.parent, level, 0};
-      StagedSink sink{QueueOut{P.q[qb ^ 1], P.qoff[qb ^ 1], P.cs[qb ^ 1], outc, (uint32_t)g.n,
-                               P.cs_cap},
-                      ctl};
-      // every queued vertex has degree >= 2
-      const int s = chunk_shift(D, (uint32_t)P.bmax, 2u);
+      StagedSink sink{QueueOut{P.q[qb ^ 1], P.qoff[qb ^ 1], P.qadj[qb ^ 1], P.cs[qb ^ 1], outc,
+                               (uint32_t)g.n, P.cs_cap},
+                      ctl, nullptr};
+      // chunks of at most 2 bmax edges: every queued vertex has degree >= 2,
+      // so a chunk is one piece and a walk step never overfills the stage
+      const int s = chunk_shift(D, 4u, chunk_shift_cap((uint32_t)P.bmax * 2u));
       blocked_edge_map(g, in, s, (uint32_t)P.bmax, S, fn, sink, ctl, bem++);
       sink.finish(S);
       reached += fn.reached;
@@ -545,6 +548,7 @@ gbf_status launch_bfs(Graph &g, Workspace &ws, int32_t src, int32_t *dist, int32
   for (int i = 0; i < 2; i++) {
     P.q[i] = ws.q[i];
     P.qoff[i] = ws.qoff[i];
+    P.qadj[i] = ws.qadj[i];
     P.cs[i] = ws.cs[i];
   }
   P.cs_cap = (uint32_t)(((uint64_t)g.m + kFine - 1) / kFine + 2);
@@ -560,7 +564,7 @@ gbf_status launch_bfs(Graph &g, Workspace &ws, int32_t src, int32_t *dist, int32
   P.pull_serial = o.pull_serial;
   P.inject_wait = o.inject_wait;
   P.cap_ns = o.spin_cap_ns;
-  const size_t smem = push_smem_bytes(SmemShape{P.bmax, P.cap, 0, 0});
+  const size_t smem = push_smem_bytes(SmemShape{P.bmax, P.cap, 0, 0, 1});
   {
     const gbf_status sm = check_smem(smem, "bfs_kernel");
     if (sm != GBF_OK) return sm;
@@ -587,7 +591,7 @@ gbf_status launch_bfs(Graph &g, Workspace &ws, int32_t src, int32_t *dist, int32
 }
 
 int resident_ctas_per_sm_bfs(const Opts &o) {
-  const size_t smem = push_smem_bytes(SmemShape{o.heavy_cutoff, stage_capacity(o.block), 0, 0});
+  const size_t smem = push_smem_bytes(SmemShape{o.heavy_cutoff, stage_capacity(o.block), 0, 0, 1});
   if (cudaFuncSetAttribute(bfs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return 0;

@@ -178,6 +178,8 @@ constexpr int kU = 4;  // 32-edge windows a warp keeps in flight per step
 //                          its first arc
 //   out_v/out_d [cap]      staged next-frontier vertices and their degrees
 //   pref        [cap]      exclusive prefix of out_d (or ranks) during a flush
+//   out_a       [cap]      CSR offset of each staged vertex's first arc (only
+//                          for queues that carry it)
 //   fv/fs       [cap]      staged bucket filings: vertex, slot (<0: overflow)
 //   hist/gbase  [nB]       per-slot counts and reserved positions of a flush
 struct PushSmem {
@@ -187,6 +189,7 @@ struct PushSmem {
   int32_t *out_v;
   uint32_t *out_d;
   uint32_t *pref;
+  uint32_t *out_a;
   int32_t *fv;
   int32_t *fs;
   uint32_t *hist;
@@ -207,14 +210,15 @@ __host__ __device__ inline int stage_capacity(int block) {
 }
 
 struct SmemShape {
-  int bmax;   // largest chunk of the blocked edgeMap
+  int bmax;   // largest piece of the blocked edgeMap
   int cap;    // staging capacity (stage_capacity(blockDim))
   int filed;  // 1: reserve the bucket-filing stage
   int nB;     // bucket slots (histogram size)
+  int adj;    // 1: stage first-arc offsets (queues with an adj array)
 };
 
 __host__ __device__ inline size_t push_smem_bytes(const SmemShape &sh) {
-  size_t w = 64 + 3 * (size_t)(sh.bmax + 2) + 3 * (size_t)sh.cap;
+  size_t w = 64 + 3 * (size_t)(sh.bmax + 2) + (sh.adj ? 4 : 3) * (size_t)sh.cap;
   if (sh.filed) w += 2 * (size_t)sh.cap + 2 * (size_t)sh.nB;
   return 8 * 32 + 4 * w + 16;
 }
@@ -238,6 +242,11 @@ __device__ __forceinline__ PushSmem carve_push_smem(void *raw, const SmemShape &
   p += sh.cap;
   S.pref = p;
   p += sh.cap;
+  S.out_a = nullptr;
+  if (sh.adj) {
+    S.out_a = p;
+    p += sh.cap;
+  }
   S.fv = S.fs = nullptr;
   S.hist = S.gbase = nullptr;
   if (sh.filed) {
@@ -253,8 +262,10 @@ __device__ __forceinline__ PushSmem carve_push_smem(void *raw, const SmemShape &
   return S;
 }
 
-// Warp-collective: append the lanes with emit set to the CTA staging buffer.
-__device__ __forceinline__ void stage_append(PushSmem &S, bool emit, int32_t v, uint32_t d) {
+// Warp-collective: append the lanes with emit set to the CTA staging buffer
+// (vertex, degree, CSR offset of its first arc).
+__device__ __forceinline__ void stage_append(PushSmem &S, bool emit, int32_t v, uint32_t d,
+                                             uint32_t a) {
   unsigned bal = __ballot_sync(kFull, emit);
   if (bal == 0) return;
   const int lane = threadIdx.x & 31;
@@ -266,13 +277,16 @@ __device__ __forceinline__ void stage_append(PushSmem &S, bool emit, int32_t v, 
     uint32_t r = pos + __popc(bal & lanemask_lt());
     S.out_v[r] = v;
     S.out_d[r] = d;
+    if (S.out_a) S.out_a[r] = a;
   }
 }
 
-// Output frontier description (sparse vertexSubset with degree prefix).
+// Output frontier description (sparse vertexSubset with degree prefix and,
+// if adj is set, the CSR offset of every entry's first arc).
 struct QueueOut {
   int32_t *q;
   uint32_t *qoff;
+  uint32_t *adj;
   uint32_t *cs;
   unsigned long long *counter;  // (count << 32) | degree sum, reserved per flush
   uint32_t q_cap;
@@ -283,11 +297,23 @@ struct QueueOut {
 // atomicAdd reserves both the queue range and the edge-space range, so the
 // per-entry degree prefix (qoff) is globally consistent; every chunk start
 // (multiple of 256 edges) falling in an entry's range records the entry.
-__device__ __forceinline__ void stage_flush(PushSmem &S, const QueueOut &out, Ctl *ctl) {
+// With off given, the entries were staged as vertices only and their degree
+// and first-arc offset are read here, many loads in flight at once.
+__device__ __forceinline__ void stage_flush(PushSmem &S, const QueueOut &out, Ctl *ctl,
+                                            const uint32_t *off = nullptr) {
   __syncthreads();
   const uint32_t k = min(S.misc[0], S.cap_out);  // entries beyond cap were spilled
   if (k == 0) return;
   const uint32_t tid = threadIdx.x, bd = blockDim.x;
+  if (off) {
+    for (uint32_t i = tid; i < k; i += bd) {
+      const int32_t v = S.out_v[i];
+      const uint32_t a = __ldg(off + v);
+      S.out_d[i] = __ldg(off + v + 1) - a;
+      if (S.out_a) S.out_a[i] = a;
+    }
+    __syncthreads();
+  }
   const uint32_t per = (k + bd - 1) / bd;
   const uint32_t lo = min(k, tid * per), hi = min(k, lo + per);
   uint32_t loc = 0;
@@ -316,6 +342,7 @@ __device__ __forceinline__ void stage_flush(PushSmem &S, const QueueOut &out, Ct
     for (uint32_t i = tid; i < k; i += bd) {
       out.q[pos + i] = S.out_v[i];
       out.qoff[pos + i] = dpos + S.pref[i];
+      if (out.adj) out.adj[pos + i] = S.out_a[i];
     }
     // chunk starts (multiples of 256) inside [dpos, dpos + total), spread over
     // the CTA: each finds its entry by binary search of the staged prefix
@@ -352,6 +379,7 @@ __device__ __forceinline__ void stage_make_room(PushSmem &S, const QueueOut &out
 struct QueueIn {
   const int32_t *q;
   const uint32_t *qoff;
+  const uint32_t *adj;
   const uint32_t *cs;
   uint32_t cnt;  // entries
   uint32_t D;    // degree sum (frontier edges)
@@ -425,13 +453,15 @@ __device__ __forceinline__ void walk_chunk(PushSmem &S, uint32_t m, uint32_t nv,
 
 // Blocked sparse edgeMap over the frontier `in` with chunks of B = 256 << s
 // edges located through the chunk-start table (edgeMapBlocked, Alg. 2).  A
-// chunk may span at most bmax + 1 frontier vertices (the shared arrays);
-// callers bound s by the smallest degree in the queue.  Each CTA starts with
-// chunk blockIdx.x and then takes chunks from a global counter, so CTAs that
-// finish early take up the slack of slow ones before the round's barrier.
-// `inv` numbers the calls of a launch (identically in every CTA): call inv
-// uses counter ctl->work[inv % 4] and clears ctl->work[(inv + 2) % 4], whose
-// last user finished before at least one grid barrier.
+// chunk's frontier vertices are loaded into the shared arrays bmax at a time
+// and each piece's share of the chunk's edges is walked before the next
+// piece is loaded, so the chunk size does not depend on the degrees.  Each
+// CTA starts with chunk blockIdx.x and then takes chunks from a global
+// counter, so CTAs that finish early take up the slack of slow ones before
+// the round's barrier.  `inv` numbers the calls of a launch (identically in
+// every CTA): call inv uses counter ctl->work[inv % 4] and clears
+// ctl->work[(inv + 2) % 4], whose last user finished before at least one
+// grid barrier.
 template <class Fn, class Sink>
 __device__ __forceinline__ void blocked_edge_map(const DevGraph &g, const QueueIn &in, int s,
                                                  uint32_t bmax, PushSmem &S, Fn &fn, Sink &sink,
@@ -447,33 +477,42 @@ __device__ __forceinline__ void blocked_edge_map(const DevGraph &g, const QueueI
     const uint32_t f1 = (c + 1) << s;
     const uint32_t i0 = in.cs[c << s];
     const uint32_t i1 = (f1 < nfine) ? in.cs[f1] : in.cnt - 1;
-    const bool bad = i1 < i0 || i1 >= in.cnt || i1 - i0 > bmax;  // never expected
+    const bool bad = i1 < i0 || i1 >= in.cnt;  // never expected
     if (bad && threadIdx.x == 0) raise_error(ctl, GBF_ERR_OVERFLOW, 3);
-    const uint32_t nv = bad ? 0u : i1 - i0 + 1;
-    for (uint32_t j = threadIdx.x; j < nv; j += blockDim.x) {
-      int32_t u = in.q[i0 + j];
-      S.base[j] = in.qoff[i0 + j];
-      S.u[j] = u;
-      S.adj[j] = __ldg(g.off + u);
-    }
-    if (threadIdx.x == 0 && nv) S.base[nv] = (i1 + 1 < in.cnt) ? in.qoff[i1 + 1] : in.D;
     // The next chunk for this CTA, taken while the current one is walked.
-    // Two slots: a thread may still be reading the previous iteration's
-    // slot when thread 0 writes this one (at most one iteration apart, as
-    // every iteration holds a __syncthreads).
+    // Two slots: a thread may still be reading the previous chunk's slot
+    // when thread 0 writes this one (at most one chunk apart, as every
+    // piece holds a __syncthreads).
     if (threadIdx.x == 0) S.misc[48 + (it & 1)] = gridDim.x + atomicAdd(work, 1u);
-    __syncthreads();
-    if (nv) walk_chunk(S, g.m, nv, e_lo, e_hi, fn, sink);
-    sink.chunk_end(S);  // starts with __syncthreads
+    const uint32_t iend = bad ? i0 : i1 + 1;
+    for (uint32_t p0 = i0; p0 < iend; p0 += bmax) {  // CTA-uniform
+      const uint32_t nv = min(bmax, iend - p0);
+      for (uint32_t j = threadIdx.x; j < nv; j += blockDim.x) {
+        const int32_t u = in.q[p0 + j];
+        S.base[j] = in.qoff[p0 + j];
+        S.u[j] = u;
+        S.adj[j] = in.adj ? in.adj[p0 + j] : __ldg(g.off + u);
+      }
+      if (threadIdx.x == 0) S.base[nv] = (p0 + nv < in.cnt) ? in.qoff[p0 + nv] : in.D;
+      __syncthreads();
+      const uint32_t lo = max(e_lo, S.base[0]), hi = min(e_hi, S.base[nv]);
+      if (lo < hi) walk_chunk(S, g.m, nv, lo, hi, fn, sink);
+      sink.chunk_end(S);  // starts with __syncthreads
+    }
+    if (iend == i0) __syncthreads();  // the slot write above is read below
     c = S.misc[48 + (it & 1)];
   }
 }
 
 // Warp-collective: stage the lanes with emit set; an entry that finds the
 // stage full is written straight to the output queue (reserving its own
-// count and edge range, then its chunk starts).
+// count and edge range, then its chunk starts).  With off given the entry's
+// degree and first-arc offset are read from the CSR (at flush time for
+// staged entries, here for spilled ones) and d, a are ignored.
 __device__ __forceinline__ void stage_append_or_spill(PushSmem &S, bool emit, int32_t v,
-                                                      uint32_t d, const QueueOut &out, Ctl *ctl) {
+                                                      uint32_t d, uint32_t a,
+                                                      const QueueOut &out, Ctl *ctl,
+                                                      const uint32_t *off) {
   const unsigned bal = __ballot_sync(kFull, emit);
   if (bal == 0) return;
   const int lane = threadIdx.x & 31;
@@ -486,44 +525,58 @@ __device__ __forceinline__ void stage_append_or_spill(PushSmem &S, bool emit, in
   if (r < S.cap_out) {
     S.out_v[r] = v;
     S.out_d[r] = d;
+    if (S.out_a) S.out_a[r] = a;
     return;
   }
+  if (off) {
+    a = __ldg(off + v);
+    d = __ldg(off + v + 1) - a;
+  }
   const unsigned long long old = atomicAdd(out.counter, (1ull << 32) | d);
-  const uint32_t qp = (uint32_t)(old >> 32), a = (uint32_t)old;
+  const uint32_t qp = (uint32_t)(old >> 32), e0 = (uint32_t)old;
   if (qp >= out.q_cap) {
     raise_error(ctl, GBF_ERR_OVERFLOW, 11);
     return;
   }
   out.q[qp] = v;
-  out.qoff[qp] = a;
-  for (uint32_t c = (a + kFine - 1) >> kFineLog; (c << kFineLog) < a + d; c++)
+  out.qoff[qp] = e0;
+  if (out.adj) out.adj[qp] = a;
+  for (uint32_t c = (e0 + kFine - 1) >> kFineLog; (c << kFineLog) < e0 + d; c++)
     if (c < out.cs_cap) out.cs[c] = qp;
 }
 
-// Sink that stages into shared memory and flushes into a QueueOut.
+// Sink that stages into shared memory and flushes into a QueueOut.  With
+// off given, callers append vertices only (d, a ignored) and the degrees and
+// first-arc offsets are read when the stage is flushed.
 struct StagedSink {
   QueueOut out;
   Ctl *ctl;
-  __device__ __forceinline__ void append(PushSmem &S, bool emit, int32_t v, uint32_t d) {
-    stage_append_or_spill(S, emit, v, d, out, ctl);
+  const uint32_t *off;
+  __device__ __forceinline__ void append(PushSmem &S, bool emit, int32_t v, uint32_t d,
+                                         uint32_t a) {
+    stage_append_or_spill(S, emit, v, d, a, out, ctl, off);
   }
   // CTA-collective, between chunks
   __device__ __forceinline__ void chunk_end(PushSmem &S) {
     __syncthreads();
-    if (S.misc[0] > (S.cap_out >> 1)) stage_flush(S, out, ctl);
+    if (S.misc[0] > (S.cap_out >> 1)) stage_flush(S, out, ctl, off);
   }
-  __device__ __forceinline__ void finish(PushSmem &S) { stage_flush(S, out, ctl); }
+  __device__ __forceinline__ void finish(PushSmem &S) { stage_flush(S, out, ctl, off); }
 };
 
-// Chunk exponent s (chunk = 256 << s edges) for a frontier of D edges whose
-// vertices all have at least min_deg edges: about four chunks per CTA, and a
-// chunk never spans more than bmax + 1 vertices (B <= bmax * min_deg), nor
-// more than 2^16 edges.
-__device__ __forceinline__ int chunk_shift(uint32_t D, uint32_t bmax, uint32_t min_deg) {
-  const uint32_t per = D / (4u * gridDim.x);
-  const unsigned long long cap = min((unsigned long long)bmax * max(min_deg, 1u), 65536ull);
+// Chunk exponent s (chunk = 256 << s edges) for a frontier of D edges:
+// about `per_cta` chunks per CTA (the counter balances them), s <= max_s.
+__device__ __forceinline__ int chunk_shift(uint32_t D, uint32_t per_cta, int max_s) {
+  const uint32_t per = D / (per_cta * gridDim.x);
   int s = 0;
-  while ((unsigned long long)(kFine << (s + 1)) <= cap && (kFine << s) < per) s++;
+  while (s < max_s && (kFine << s) < per) s++;
+  return s;
+}
+
+// Largest s with chunks of 256 << s edges not above `edges` (and 2^16).
+__device__ __forceinline__ int chunk_shift_cap(uint32_t edges) {
+  int s = 0;
+  while (s < 8 && (kFine << (s + 1)) <= edges) s++;
   return s;
 }
 

@@ -78,6 +78,7 @@ struct Workspace {
   uint32_t *fbm[3] = {nullptr, nullptr, nullptr};
   int32_t *q[2] = {nullptr, nullptr};
   uint32_t *qoff[2] = {nullptr, nullptr};
+  uint32_t *qadj[2] = {nullptr, nullptr};  // CSR offset of each entry's first arc
   uint32_t *cs[2] = {nullptr, nullptr};  // chunk starts, one per 256 frontier edges
   Ctl *ctl = nullptr;
   int32_t *dist_tmp = nullptr;     // used for host-memory outputs
@@ -94,6 +95,7 @@ struct Workspace {
   unsigned long long *ms_seen = nullptr, *ms_visit = nullptr, *ms_next = nullptr;
   int32_t *ms_q[3] = {nullptr, nullptr, nullptr};
   uint32_t *ms_qoff[3] = {nullptr, nullptr, nullptr};
+  uint32_t *ms_qadj[3] = {nullptr, nullptr, nullptr};
   uint32_t *ms_cs[3] = {nullptr, nullptr, nullptr};
   int32_t *ms_touched = nullptr;
   void *ms_call = nullptr;        // device parameter block

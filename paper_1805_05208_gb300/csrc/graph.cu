@@ -195,6 +195,7 @@ gbf_status ws_ensure_base(Graph &g, Workspace &ws) {
     GBF_TRY(dmalloc(&ws.fbm[i], nw, acc));
     GBF_TRY(dmalloc(&ws.q[i], n, acc));
     GBF_TRY(dmalloc(&ws.qoff[i], n, acc));
+    GBF_TRY(dmalloc(&ws.qadj[i], n, acc));
     GBF_TRY(dmalloc(&ws.cs[i], cs, acc));
   }
   GBF_TRY(dmalloc(&ws.dist_tmp, n, acc));
@@ -255,6 +256,7 @@ gbf_status ws_ensure_msbfs(Graph &g, Workspace &ws, bool host_out) {
     GBF_TRY(dmalloc(&ws.ms_next, n, acc));
     GBF_TRY(dmalloc(&ws.ms_q[2], n, acc));
     GBF_TRY(dmalloc(&ws.ms_qoff[2], n, acc));
+    GBF_TRY(dmalloc(&ws.ms_qadj[2], n, acc));
     GBF_TRY(dmalloc(&ws.ms_cs[2], cs, acc));
     GBF_TRY(dmalloc(&ws.ms_touched, n, acc));
     char *call = nullptr;
@@ -263,6 +265,7 @@ gbf_status ws_ensure_msbfs(Graph &g, Workspace &ws, bool host_out) {
     for (int i = 0; i < 2; i++) {
       ws.ms_q[i] = ws.q[i];
       ws.ms_qoff[i] = ws.qoff[i];
+      ws.ms_qadj[i] = ws.qadj[i];
       ws.ms_cs[i] = ws.cs[i];
     }
     GBF_CUDA(cudaMallocHost(&ws.ms_call_host, 1024));
@@ -277,6 +280,7 @@ gbf_status ws_ensure_msbfs(Graph &g, Workspace &ws, bool host_out) {
 
 void ws_free(Workspace &ws) {
   void *ptrs[] = {ws.visited, ws.fbm[0], ws.fbm[1], ws.fbm[2], ws.q[0], ws.q[1], ws.qoff[0], ws.qoff[1],
+                  ws.qadj[0], ws.qadj[1], ws.ms_qadj[2],
                   ws.cs[0], ws.cs[1], ws.ctl, ws.dist_tmp, ws.parent_tmp, ws.trace, ws.slots,
                   ws.slot_cnt, ws.ovf[0], ws.ovf[1], ws.ms_seen, ws.ms_visit, ws.ms_next,
                   ws.ms_q[2], ws.ms_qoff[2], ws.ms_cs[2], ws.ms_touched, ws.ms_call,

@@ -45,6 +45,7 @@ struct MsParams {
   unsigned long long *next;
   int32_t *q[3];
   uint32_t *qoff[3];
+  uint32_t *qadj[3];
   uint32_t *cs[3];
   uint32_t cs_cap;
   int32_t *touched;
@@ -139,7 +140,7 @@ struct MsPushFn {
 __global__ void __launch_bounds__(1024) msbfs_kernel(MsParams P) {
   extern __shared__ unsigned long long smem_raw[];
   __shared__ int s_flag;
-  PushSmem S = carve_push_smem(smem_raw, SmemShape{P.bmax, P.cap, 0, 0});
+  PushSmem S = carve_push_smem(smem_raw, SmemShape{P.bmax, P.cap, 0, 0, 1});
   if (threadIdx.x == 0) S.misc[0] = 0;
   Ctl *ctl = P.ctl;
   Barrier bar{0u, P.cap_ns};
@@ -166,7 +167,7 @@ __global__ void __launch_bounds__(1024) msbfs_kernel(MsParams P) {
   if (ok && blockIdx.x == 0) {
     bool emit = false;
     int32_t s = 0;
-    uint32_t d = 0;
+    uint32_t d = 0, a = 0;
     if ((int)threadIdx.x < k) {
       s = P.call->srcs[threadIdx.x];
       atomicOr(P.seen + s, 1ull << threadIdx.x);
@@ -174,11 +175,12 @@ __global__ void __launch_bounds__(1024) msbfs_kernel(MsParams P) {
       rows[threadIdx.x][s] = 0;
       bool dup = false;
       for (int j = 0; j < (int)threadIdx.x; j++) dup |= P.call->srcs[j] == s;
-      d = __ldg(g.off + s + 1) - __ldg(g.off + s);
+      a = __ldg(g.off + s);
+      d = __ldg(g.off + s + 1) - a;
       emit = !dup && d > 0;
     }
-    stage_append(S, emit, s, d);  // whole CTA: warp-collective
-    stage_flush(S, QueueOut{P.q[0], P.qoff[0], P.cs[0], &ctl->fr[0], n, P.cs_cap}, ctl);
+    stage_append(S, emit, s, d, a);  // whole CTA: warp-collective
+    stage_flush(S, QueueOut{P.q[0], P.qoff[0], P.qadj[0], P.cs[0], &ctl->fr[0], n, P.cs_cap}, ctl);
     if (threadIdx.x == 0) reached = (unsigned long long)k;
   }
   ok = ok && grid_sync(ctl, bar, &s_flag);
@@ -201,7 +203,7 @@ __global__ void __launch_bounds__(1024) msbfs_kernel(MsParams P) {
       atomicAdd(&ctl->rounds, 1);
       atomicAdd(dense ? &ctl->pull_rounds : &ctl->push_rounds, 1);
     }
-    QueueOut fout{P.q[qn], P.qoff[qn], P.cs[qn], outc, n, P.cs_cap};
+    QueueOut fout{P.q[qn], P.qoff[qn], P.qadj[qn], P.cs[qn], outc, n, P.cs_cap};
     if (!dense) {
       // nxt still holds the frontier of level L-2 (queue qo, plus every
       // source when L == 2): clear it while the push reads cur
@@ -210,10 +212,10 @@ __global__ void __launch_bounds__(1024) msbfs_kernel(MsParams P) {
         for (uint32_t i = gt; i < c2; i += gs) nxt[P.q[qo][i]] = 0ull;
         if (L == 2 && blockIdx.x == 0 && (int)threadIdx.x < k) nxt[P.call->srcs[threadIdx.x]] = 0ull;
       }
-      QueueIn in{P.q[qc], P.qoff[qc], P.cs[qc], cnt, D};
+      QueueIn in{P.q[qc], P.qoff[qc], P.qadj[qc], P.cs[qc], cnt, D};
       MsPushFn fn{g.tgt, cur, P.seen, P.next, 0};
       TouchSink sink{P.touched, tcount, n, ctl};
-      blocked_edge_map(g, in, chunk_shift(D, (uint32_t)P.bmax, 1u), (uint32_t)P.bmax, S, fn, sink,
+      blocked_edge_map(g, in, chunk_shift(D, 4u, 8), (uint32_t)P.bmax, S, fn, sink,
                        ctl, bem++);
       if (blockIdx.x == 0 && threadIdx.x == 0) {
         scanned += D;
@@ -227,7 +229,7 @@ __global__ void __launch_bounds__(1024) msbfs_kernel(MsParams P) {
         const uint32_t i = it + threadIdx.x;
         int32_t v = 0;
         u64 nwb = 0;
-        uint32_t d = 0;
+        uint32_t d = 0, a = 0;
         if (i < tc) {
           v = P.touched[i];
           const u64 x = P.next[v];
@@ -236,7 +238,8 @@ __global__ void __launch_bounds__(1024) msbfs_kernel(MsParams P) {
           if (nwb) {
             P.seen[v] |= nwb;
             nxt[v] = nwb;
-            d = __ldg(g.off + v + 1) - __ldg(g.off + v);
+            a = __ldg(g.off + v);
+            d = __ldg(g.off + v + 1) - a;
             reached += __popcll(nwb);
           }
         }
@@ -247,7 +250,7 @@ __global__ void __launch_bounds__(1024) msbfs_kernel(MsParams P) {
           bits &= bits - 1;
           if (bi < k) rows[bi][v] = L;
         }
-        stage_append(S, nwb != 0ull && d > 0, v, d);
+        stage_append(S, nwb != 0ull && d > 0, v, d, a);
         __syncthreads();
         stage_make_room(S, fout, ctl, blockDim.x);
       }
@@ -309,7 +312,7 @@ __global__ void __launch_bounds__(1024) msbfs_kernel(MsParams P) {
         }
         if (cand) expanded++;
         write_rows(rows, k, v, inr ? nwb : 0ull, L);
-        stage_append(S, nwb != 0ull && e > s, v, e - s);
+        stage_append(S, nwb != 0ull && e > s, v, e - s, s);
         __syncthreads();
         stage_make_room(S, fout, ctl, blockDim.x);
       }
@@ -373,6 +376,7 @@ gbf_status launch_msbfs_rows(Graph &g, Workspace &ws, const int32_t *srcs_host, 
     for (int i = 0; i < 3; i++) {
       P.q[i] = ws.ms_q[i];
       P.qoff[i] = ws.ms_qoff[i];
+      P.qadj[i] = ws.ms_qadj[i];
       P.cs[i] = ws.ms_cs[i];
     }
     P.cs_cap = (uint32_t)(((uint64_t)ws.m + kFine - 1) / kFine + 2);
@@ -386,7 +390,7 @@ gbf_status launch_msbfs_rows(Graph &g, Workspace &ws, const int32_t *srcs_host, 
     P.cap = stage_capacity(o.block);
     P.inject_wait = o.inject_wait;
     P.cap_ns = o.spin_cap_ns;
-    const size_t smem = push_smem_bytes(SmemShape{P.bmax, P.cap, 0, 0});
+    const size_t smem = push_smem_bytes(SmemShape{P.bmax, P.cap, 0, 0, 1});
     {
     const gbf_status sm = check_smem(smem, "msbfs_kernel");
     if (sm != GBF_OK) return sm;
@@ -445,7 +449,7 @@ gbf_status launch_msbfs(Graph &g, Workspace &ws, const int32_t *srcs_host, int32
 }
 
 int resident_ctas_per_sm_msbfs(const Opts &o) {
-  const size_t smem = push_smem_bytes(SmemShape{o.heavy_cutoff, stage_capacity(o.block), 0, 0});
+  const size_t smem = push_smem_bytes(SmemShape{o.heavy_cutoff, stage_capacity(o.block), 0, 0, 1});
   if (cudaFuncSetAttribute(msbfs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return 0;

@@ -27,7 +27,7 @@ constexpr size_t kBitW = words256((size_t)kMaxN / 32);
 constexpr size_t kQW = words256((size_t)kMaxN);
 constexpr size_t kCsW = words256((size_t)(kMaxM / dev::kFine) + 2);
 constexpr size_t kCtlW = words256((sizeof(Ctl) + 3) / 4);
-constexpr size_t kScratchWords = 4 * kBitW + 4 * kQW + 2 * kCsW + kCtlW;  // ~18.3 MB
+constexpr size_t kScratchWords = 4 * kBitW + 6 * kQW + 2 * kCsW + kCtlW;  // ~26.7 MB
 
 static __device__ __align__(256) uint32_t g_scratch[kScratchWords];
 
@@ -113,6 +113,10 @@ extern "C" gbf_status gbf_bfs_noalloc(int32_t n, uint32_t m, const uint32_t *off
   ws.qoff[0] = p;
   p += kQW;
   ws.qoff[1] = p;
+  p += kQW;
+  ws.qadj[0] = p;
+  p += kQW;
+  ws.qadj[1] = p;
   p += kQW;
   ws.cs[0] = p;
   p += kCsW;

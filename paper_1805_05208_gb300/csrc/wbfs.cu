@@ -411,7 +411,7 @@ __global__ void __launch_bounds__(1024) wbfs_kernel(WbfsParams P) {
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&ctl->push_rounds, 1);
     // ---------------- edgeMapData over the live entries of bucket b
-    QueueOut fout{P.q, P.qoff, P.cs, fctr, (uint32_t)g.n, P.cs_cap};
+    QueueOut fout{P.q, P.qoff, nullptr, P.cs, fctr, (uint32_t)g.n, P.cs_cap};
     RelaxFn fn{g.tgt, g.w, P.dist, b, 0};
     const int32_t *sl = P.slots + (size_t)sb * (size_t)g.n;
     for (uint32_t it = blockIdx.x * blockDim.x; it < cntb; it += gs) {
@@ -430,7 +430,7 @@ __global__ void __launch_bounds__(1024) wbfs_kernel(WbfsParams P) {
         }
       }
       const bool heavy = live && deg > (uint32_t)P.heavy;
-      stage_append(S, heavy, v, deg);
+      stage_append(S, heavy, v, deg, a0);
       const bool light = live && !heavy;
       if (live) c.expanded++;
       if (heavy) c.heavy++;
@@ -463,9 +463,9 @@ __global__ void __launch_bounds__(1024) wbfs_kernel(WbfsParams P) {
     const long long t_mid = (long long)(globaltimer() - t_start);
     if (hcnt > 0) {
       // heavy vertices of the bucket: blocked edgeMap over all CTAs
-      QueueIn in{P.q, P.qoff, P.cs, hcnt, hD};
+      QueueIn in{P.q, P.qoff, nullptr, P.cs, hcnt, hD};
       // every heavy vertex has more than P.heavy edges
-      blocked_edge_map(g, in, chunk_shift(hD, (uint32_t)P.bmax, (uint32_t)P.heavy + 1u),
+      blocked_edge_map(g, in, chunk_shift(hD, 4u, 7),
                        (uint32_t)P.bmax, S, fn, fsink, ctl, bem++);
       fsink.flush(S);
       if (blockIdx.x == 0 && threadIdx.x == 0) c.scanned += hD;
