@@ -19,6 +19,8 @@ reference) on bounded samples of the same workload instead.
 from __future__ import annotations
 
 import argparse
+import glob
+import hashlib
 import json
 import os
 import statistics
@@ -163,6 +165,32 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def kernel_source_hash():
+    """Short hash of the CUDA sources (csrc/): a DRAM-traffic figure taken
+    with ncu is only reported while the kernels it measured are unchanged."""
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1805_05208_gb300", "csrc", "*"))):
+        with open(p, "rb") as f:
+            h.update(os.path.basename(p).encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload, kernel):
+    """dram__bytes_read.sum + dram__bytes_write.sum per launch of `kernel` on
+    `workload` from profiles/traffic.json (written from an ncu capture), or
+    None if there is none for the current sources."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            table = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = table.get(workload)
+    if not e or e.get("kernel") != kernel or e.get("csrc_hash") != kernel_source_hash():
+        return None
+    return e.get("bytes_per_launch")
 
 
 def bytes_model(kind, n, st):
@@ -478,7 +506,8 @@ def run_msbfs(args, wl, g, srcs, graph, opt, stream, dev, rank, world, barrier, 
             "roofline": {"bound": "hbm", "kernel": "msbfs_kernel", "achieved": bpl / (avg / 1e3) / 1e9,
                          "peak": peak, "unit": "GB/s", "frac": bpl / (avg / 1e3) / 1e9 / peak,
                          "peak_source": f"{peak_kind} hbm_gbs (burst copy)", "bytes_per_launch": bpl,
-                         "avg_launch_ms": avg, "traffic": None},
+                         "avg_launch_ms": avg,
+                         "traffic": measured_traffic(args.workload, "msbfs_kernel")},
             "cpu_baseline": cpu,
             "e2e": {"value": te_all * e2e_steps / e2e_s / 1e9, "unit": "GTEPS",
                     "h2d_bytes_per_step": 4 * k, "d2h_bytes_per_step": 4 * k * n},
@@ -650,7 +679,7 @@ def main():
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_source": f"{peak_kind} hbm_gbs (burst copy)",
                          "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_launch_ms,
-                         "traffic": None},
+                         "traffic": measured_traffic(args.workload, f"{kind}_kernel")},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": "GTEPS", "h2d_bytes_per_step": 4 * len(srcs),
                     "d2h_bytes_per_step": d2h},

@@ -84,7 +84,7 @@ typedef struct gbf_graph gbf_graph;
  *   ctas          CTAs of the persistent kernels (default: every CTA that fits, all SMs)
  *   pull_serial   arcs each vertex checks on its own (4 at a time) before the dense step
  *                 may walk its remaining arcs with the whole warp (0 = per kind:
- *                 32 for BFS, 8 for multi-source BFS)
+ *                 128 for BFS, 8 for multi-source BFS)
  *   inject_wait   fault injection for tests: 1 = one CTA waits on a flag nothing sets,
  *                 so the first grid barrier times out and the call returns GBF_ERR_TIMEOUT
  */

@@ -55,6 +55,7 @@ namespace {
 // winner writes D and the parent.  kU windows at a time: all target loads,
 // then all bitmap loads, then the test-and-sets, then the winners' degrees.
 struct BfsPushFn {
+  static constexpr int kWin = kU;  // windows per walk step
   const uint32_t *off;
   const int32_t *tgt;
   uint32_t *visited;
@@ -64,22 +65,22 @@ struct BfsPushFn {
   template <class Sink>
   __device__ __forceinline__ void batch(const bool *val, const int32_t *u, const uint32_t *idx,
                                         Sink &sink, PushSmem &S) {
-    int32_t v[kU];
-    uint32_t wd[kU];
+    int32_t v[kWin];
+    uint32_t wd[kWin];
 #pragma unroll
-    for (int r = 0; r < kU; r++) v[r] = val[r] ? __ldg(tgt + idx[r]) : 0;
+    for (int r = 0; r < kWin; r++) v[r] = val[r] ? __ldg(tgt + idx[r]) : 0;
 #pragma unroll
-    for (int r = 0; r < kU; r++) wd[r] = val[r] ? visited[v[r] >> 5] : ~0u;
-    bool win[kU];
+    for (int r = 0; r < kWin; r++) wd[r] = val[r] ? visited[v[r] >> 5] : ~0u;
+    bool win[kWin];
 #pragma unroll
-    for (int r = 0; r < kU; r++) {
+    for (int r = 0; r < kWin; r++) {
       const uint32_t bit = 1u << (v[r] & 31);
       win[r] = false;
       if (!(wd[r] & bit)) win[r] = !(atomicOr(visited + (v[r] >> 5), bit) & bit);
     }
-    uint32_t a[kU], z[kU];
+    uint32_t a[kWin], z[kWin];
 #pragma unroll
-    for (int r = 0; r < kU; r++) {
+    for (int r = 0; r < kWin; r++) {
       a[r] = z[r] = 0;
       if (win[r]) {
         dist[v[r]] = level;
@@ -90,7 +91,7 @@ struct BfsPushFn {
       }
     }
 #pragma unroll
-    for (int r = 0; r < kU; r++) {
+    for (int r = 0; r < kWin; r++) {
       const uint32_t d = z[r] - a[r];
       sink.append(S, win[r] && d >= 2, v[r], d, a[r]);
     }
@@ -507,9 +508,10 @@ __global__ void __launch_bounds__(1024) bfs_kernel(BfsParams P) {
       StagedSink sink{QueueOut{P.q[qb ^ 1], P.qoff[qb ^ 1], P.qadj[qb ^ 1], P.cs[qb ^ 1], outc,
                                (uint32_t)g.n, P.cs_cap},
                       ctl, nullptr};
-      // chunks of at most 2 bmax edges: every queued vertex has degree >= 2,
-      // so a chunk is one piece and a walk step never overfills the stage
-      const int s = chunk_shift(D, 4u, chunk_shift_cap((uint32_t)P.bmax * 2u));
+      // chunks of one walk step of the whole CTA (kWin windows per warp):
+      // a step appends at most half the staging capacity, which chunk_end
+      // keeps free
+      const int s = chunk_shift(D, 4u, chunk_shift_cap(32u * BfsPushFn::kWin * blockDim.x));
       blocked_edge_map(g, in, s, (uint32_t)P.bmax, S, fn, sink, ctl, bem++);
       sink.finish(S);
       reached += fn.reached;

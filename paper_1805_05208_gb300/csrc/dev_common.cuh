@@ -408,19 +408,20 @@ __device__ __forceinline__ uint32_t smem_upper(const uint32_t *base, uint32_t nv
 template <class Fn, class Sink>
 __device__ __forceinline__ void walk_chunk(PushSmem &S, uint32_t m, uint32_t nv, uint32_t e_lo,
                                            uint32_t e_hi, Fn &fn, Sink &sink) {
+  constexpr int U = Fn::kWin;  // windows per step
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const uint32_t nwin = (e_hi - e_lo + 31) >> 5;
   uint32_t K = (nwin + nw - 1) / nw;
-  K = (K + kU - 1) / kU * kU;
+  K = (K + U - 1) / U * U;
   const uint32_t w_lo = e_lo + (uint32_t)warp * K * 32;
   const uint32_t w_hi = min(w_lo + K * 32, e_hi);
   uint32_t j = (w_lo < w_hi) ? smem_upper(S.base, nv, w_lo) : 0u;
-  for (uint32_t st = 0; st < K; st += kU) {
-    bool val[kU];
-    int32_t uu[kU];
-    uint32_t idx[kU];
+  for (uint32_t st = 0; st < K; st += U) {
+    bool val[U];
+    int32_t uu[U];
+    uint32_t idx[U];
 #pragma unroll
-    for (int r = 0; r < kU; r++) {
+    for (int r = 0; r < U; r++) {
       const uint32_t b = w_lo + (st + r) * 32;
       const bool live = b < w_hi;  // warp-uniform
       unsigned bpos = 0;

@@ -64,7 +64,7 @@ Opts resolve(const gbf_options *o, const Graph &g, int kind) {
   // pull_serial 0: per-kind default (the BFS pull hands long scans to a warp
   // walk only rarely; the multi-source pull after a few arcs)
   r.pull_serial = o->pull_serial > 0 ? std::min(o->pull_serial, 1 << 20)
-                                     : (kind == GBF_TUNE_MSBFS ? 8 : 32);
+                                     : (kind == GBF_TUNE_MSBFS ? 8 : 128);
   r.inject_wait = o->inject_wait ? 1 : 0;
   long long us = o->spin_cap_us > 0 ? o->spin_cap_us : d.spin_cap_us;
   r.spin_cap_ns = us * 1000LL;

@@ -106,6 +106,7 @@ struct TouchSink {
 
 // Push Update for kU windows: lanes visit[u] & ~seen[v] are OR-ed into next[v].
 struct MsPushFn {
+  static constexpr int kWin = kU;  // windows per walk step
   const int32_t *tgt;
   const u64 *cur;
   const u64 *seen;

@@ -186,6 +186,7 @@ struct FileSink {
 // Update of Alg. 3 for kU windows of arcs out of bucket b: all target and
 // weight loads, then the distance loads, then the writeMins.
 struct RelaxFn {
+  static constexpr int kWin = kU;  // windows per walk step
   const int32_t *tgt;
   const uint32_t *w;
   int32_t *dist;
