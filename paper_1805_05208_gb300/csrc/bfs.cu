@@ -508,10 +508,10 @@ __global__ void __launch_bounds__(1024) bfs_kernel(BfsParams P) {
       StagedSink sink{QueueOut{P.q[qb ^ 1], P.qoff[qb ^ 1], P.qadj[qb ^ 1], P.cs[qb ^ 1], outc,
                                (uint32_t)g.n, P.cs_cap},
                       ctl, nullptr};
-      // chunks of one walk step of the whole CTA (kWin windows per warp):
-      // a step appends at most half the staging capacity, which chunk_end
-      // keeps free
-      const int s = chunk_shift(D, 4u, chunk_shift_cap(32u * BfsPushFn::kWin * blockDim.x));
+      // chunks of one walk step of the whole CTA (kWin 32-edge windows per
+      // warp): a step appends at most half the staging capacity, which
+      // chunk_end keeps free
+      const int s = chunk_shift(D, 4u, chunk_shift_cap(BfsPushFn::kWin * blockDim.x));
       blocked_edge_map(g, in, s, (uint32_t)P.bmax, S, fn, sink, ctl, bem++);
       sink.finish(S);
       reached += fn.reached;
