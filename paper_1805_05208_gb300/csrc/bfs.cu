@@ -90,11 +90,13 @@ struct BfsPushFn {
         reached++;
       }
     }
+    bool emit[kWin];
 #pragma unroll
     for (int r = 0; r < kWin; r++) {
-      const uint32_t d = z[r] - a[r];
-      sink.append(S, win[r] && d >= 2, v[r], d, a[r]);
+      z[r] -= a[r];  // degree
+      emit[r] = win[r] && z[r] >= 2;
     }
+    sink.template append_n<kWin>(S, emit, v, z, a);
   }
 };
 

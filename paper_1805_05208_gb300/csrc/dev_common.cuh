@@ -416,6 +416,11 @@ __device__ __forceinline__ void walk_chunk(PushSmem &S, uint32_t m, uint32_t nv,
   const uint32_t w_lo = e_lo + (uint32_t)warp * K * 32;
   const uint32_t w_hi = min(w_lo + K * 32, e_hi);
   uint32_t j = (w_lo < w_hi) ? smem_upper(S.base, nv, w_lo) : 0u;
+  // vertex j (the owner of the next window's first edge), kept in registers
+  // while windows stay inside it: start in the chunk's edge space, first arc,
+  // id, and the start of vertex j + 1 (base[nv] is the end of the last one)
+  uint32_t jb = S.base[j], ja = S.adj[j], jn = S.base[j + 1];
+  int32_t ju = S.u[j];
   for (uint32_t st = 0; st < K; st += U) {
     bool val[U];
     int32_t uu[U];
@@ -424,28 +429,41 @@ __device__ __forceinline__ void walk_chunk(PushSmem &S, uint32_t m, uint32_t nv,
     for (int r = 0; r < U; r++) {
       const uint32_t b = w_lo + (st + r) * 32;
       const bool live = b < w_hi;  // warp-uniform
-      unsigned bpos = 0;
-      if (live) {
-        const uint32_t k = j + 1 + lane;
-        if (k <= nv) {
-          const uint32_t bb = S.base[k];
-          if (bb < b + 32) bpos = 1u << (bb - b);
-        }
-      }
-      const unsigned mask = __reduce_or_sync(kFull, bpos);
       const uint32_t e = b + lane;
       val[r] = live && e < w_hi;
       idx[r] = 0u;
       uu[r] = 0;
-      if (val[r]) {
-        const uint32_t jj = min(j + __popc(mask & lanemask_le()), nv - 1);
-        idx[r] = S.adj[jj] + (e - S.base[jj]);
-        uu[r] = S.u[jj];
-        val[r] = idx[r] < m;
-      }
       if (live) {
-        j += __popc(mask);
-        if (j + 1 <= nv && S.base[j + 1] <= b + 32) j++;
+        if (jn >= b + 32) {
+          // no vertex starts inside the window: all of it belongs to j
+          idx[r] = ja + (e - jb);
+          uu[r] = ju;
+        } else {
+          // vertices j+1.. that start inside the window, one bit per offset
+          unsigned bpos = 0;
+          const uint32_t k = j + 1 + lane;
+          if (k <= nv) {
+            const uint32_t bb = S.base[k];
+            if (bb < b + 32) bpos = 1u << (bb - b);
+          }
+          const unsigned mask = __reduce_or_sync(kFull, bpos);
+          const uint32_t jj = min(j + __popc(mask & lanemask_le()), nv - 1);
+          idx[r] = S.adj[jj] + (e - S.base[jj]);
+          uu[r] = S.u[jj];
+          j += __popc(mask);  // the owner of the window's last edge
+          jb = S.base[j];
+          ja = S.adj[j];
+          ju = S.u[j];
+          jn = S.base[j + 1];
+        }
+        if (jn == b + 32 && j < nv) {  // the next vertex starts with the next window
+          j++;
+          jb = jn;
+          ja = S.adj[j];
+          ju = S.u[j];
+          jn = S.base[j + 1];
+        }
+        if (val[r]) val[r] = idx[r] < m;
       }
     }
     fn.batch(val, uu, idx, sink, S);
@@ -505,6 +523,27 @@ __device__ __forceinline__ void blocked_edge_map(const DevGraph &g, const QueueI
   }
 }
 
+// One entry that found the stage full, written straight to the output
+// queue: it reserves its own count and edge range, then its chunk starts.
+__device__ __forceinline__ void stage_spill_one(PushSmem &, int32_t v, uint32_t d, uint32_t a,
+                                                const QueueOut &out, Ctl *ctl, const uint32_t *off) {
+  if (off) {
+    a = __ldg(off + v);
+    d = __ldg(off + v + 1) - a;
+  }
+  const unsigned long long old = atomicAdd(out.counter, (1ull << 32) | d);
+  const uint32_t qp = (uint32_t)(old >> 32), e0 = (uint32_t)old;
+  if (qp >= out.q_cap) {
+    raise_error(ctl, GBF_ERR_OVERFLOW, 11);
+    return;
+  }
+  out.q[qp] = v;
+  out.qoff[qp] = e0;
+  if (out.adj) out.adj[qp] = a;
+  for (uint32_t c = (e0 + kFine - 1) >> kFineLog; (c << kFineLog) < e0 + d; c++)
+    if (c < out.cs_cap) out.cs[c] = qp;
+}
+
 // Warp-collective: stage the lanes with emit set; an entry that finds the
 // stage full is written straight to the output queue (reserving its own
 // count and edge range, then its chunk starts).  With off given the entry's
@@ -529,21 +568,7 @@ __device__ __forceinline__ void stage_append_or_spill(PushSmem &S, bool emit, in
     if (S.out_a) S.out_a[r] = a;
     return;
   }
-  if (off) {
-    a = __ldg(off + v);
-    d = __ldg(off + v + 1) - a;
-  }
-  const unsigned long long old = atomicAdd(out.counter, (1ull << 32) | d);
-  const uint32_t qp = (uint32_t)(old >> 32), e0 = (uint32_t)old;
-  if (qp >= out.q_cap) {
-    raise_error(ctl, GBF_ERR_OVERFLOW, 11);
-    return;
-  }
-  out.q[qp] = v;
-  out.qoff[qp] = e0;
-  if (out.adj) out.adj[qp] = a;
-  for (uint32_t c = (e0 + kFine - 1) >> kFineLog; (c << kFineLog) < e0 + d; c++)
-    if (c < out.cs_cap) out.cs[c] = qp;
+  stage_spill_one(S, v, d, a, out, ctl, off);
 }
 
 // Sink that stages into shared memory and flushes into a QueueOut.  With
@@ -556,6 +581,39 @@ struct StagedSink {
   __device__ __forceinline__ void append(PushSmem &S, bool emit, int32_t v, uint32_t d,
                                          uint32_t a) {
     stage_append_or_spill(S, emit, v, d, a, out, ctl, off);
+  }
+  // Warp-collective: the U appends of one walk step with one shared-memory
+  // atomic for the whole warp.
+  template <int U>
+  __device__ __forceinline__ void append_n(PushSmem &S, const bool *emit, const int32_t *v,
+                                           const uint32_t *d, const uint32_t *a) {
+    unsigned bal[U];
+    uint32_t tot = 0;
+#pragma unroll
+    for (int r = 0; r < U; r++) {
+      bal[r] = __ballot_sync(kFull, emit[r]);
+      tot += __popc(bal[r]);
+    }
+    if (tot == 0) return;
+    const int lane = threadIdx.x & 31;
+    uint32_t pos = 0;
+    if (lane == 0) pos = atomicAdd(&S.misc[0], tot);
+    pos = __shfl_sync(kFull, pos, 0);
+    const unsigned lt = lanemask_lt();
+#pragma unroll
+    for (int r = 0; r < U; r++) {
+      if (emit[r]) {
+        const uint32_t i = pos + __popc(bal[r] & lt);
+        if (i < S.cap_out) {
+          S.out_v[i] = v[r];
+          S.out_d[i] = d[r];
+          if (S.out_a) S.out_a[i] = a[r];
+        } else {
+          stage_spill_one(S, v[r], d[r], a[r], out, ctl, off);
+        }
+      }
+      pos += __popc(bal[r]);
+    }
   }
   // CTA-collective, between chunks
   __device__ __forceinline__ void chunk_end(PushSmem &S) {

@@ -101,6 +101,33 @@ struct TouchSink {
       else raise_error(ctl, GBF_ERR_OVERFLOW, 10);
     }
   }
+  // Warp-collective: the U appends of one walk step with one atomic.
+  template <int U>
+  __device__ __forceinline__ void append_n(PushSmem &, const bool *emit, const int32_t *v,
+                                           const uint32_t *, const uint32_t *) {
+    unsigned bal[U];
+    uint32_t tot = 0;
+#pragma unroll
+    for (int r = 0; r < U; r++) {
+      bal[r] = __ballot_sync(kFull, emit[r]);
+      tot += __popc(bal[r]);
+    }
+    if (tot == 0) return;
+    const int lane = threadIdx.x & 31;
+    uint32_t pos = 0;
+    if (lane == 0) pos = atomicAdd(count, tot);
+    pos = __shfl_sync(kFull, pos, 0);
+    const unsigned lt = lanemask_lt();
+#pragma unroll
+    for (int r = 0; r < U; r++) {
+      if (emit[r]) {
+        const uint32_t i = pos + __popc(bal[r] & lt);
+        if (i < cap) list[i] = v[r];
+        else raise_error(ctl, GBF_ERR_OVERFLOW, 10);
+      }
+      pos += __popc(bal[r]);
+    }
+  }
   __device__ __forceinline__ void chunk_end(PushSmem &) { __syncthreads(); }
 };
 
@@ -132,7 +159,7 @@ struct MsPushFn {
       if (m) first[r] = atomicOr(next + v[r], m) == 0ull;
     }
 #pragma unroll
-    for (int r = 0; r < kU; r++) sink.append(S, first[r], v[r], 0u);
+    sink.template append_n<kU>(S, first, v, nullptr, nullptr);
   }
 };
 

@@ -120,6 +120,61 @@ struct FileSink {
     }
     c->inserts++;
   }
+  // The bucket slot of value nd (or -nd - 2: the overflow bucket).
+  __device__ __forceinline__ int32_t slot_of(int32_t nd) const {
+    return (P->slide || nd < lo + P->nB) ? nd % P->nB : -nd - 2;
+  }
+  // An entry that found the stage full, filed directly.
+  __device__ __forceinline__ void file_direct(int32_t v, int32_t nd, int32_t sl) {
+    if (sl >= 0) {
+      const uint32_t gp = atomicAdd(P->slot_cnt + sl, 1u) % (uint32_t)P->g.n;
+      P->slots[(size_t)sl * (size_t)P->g.n + gp] = v;
+      atomicOr(imask + (sl >> 5), 1u << (sl & 31));
+    } else {
+      const uint32_t gp = atomicAdd(&P->ctl->ovf_cnt[cur], 1u);
+      if (gp < P->ovf_cap) {
+        P->ovf[cur][gp] = make_int2(v, nd);
+        atomicMin(&P->ctl->ovf_min[cur], nd);
+      } else {
+        raise_error(P->ctl, GBF_ERR_OVERFLOW, 12);
+      }
+    }
+    c->inserts++;
+  }
+  // Warp-collective: the U filings of one walk step with one shared-memory
+  // atomic for the whole warp.
+  template <int U>
+  __device__ __forceinline__ void append_n(PushSmem &S, const bool *low, const int32_t *v,
+                                           const uint32_t *ndu, const uint32_t *) {
+    unsigned bal[U];
+    uint32_t tot = 0;
+#pragma unroll
+    for (int r = 0; r < U; r++) {
+      bal[r] = __ballot_sync(kFull, low[r]);
+      tot += __popc(bal[r]);
+    }
+    if (tot == 0) return;
+    const int lane = threadIdx.x & 31;
+    uint32_t pos = 0;
+    if (lane == 0) pos = atomicAdd(&S.misc[4], tot);
+    pos = __shfl_sync(kFull, pos, 0);
+    const unsigned lt = lanemask_lt();
+#pragma unroll
+    for (int r = 0; r < U; r++) {
+      if (low[r]) {
+        const int32_t nd = (int32_t)ndu[r];
+        const int32_t sl = slot_of(nd);
+        const uint32_t i = pos + __popc(bal[r] & lt);
+        if (i < S.cap_out) {
+          S.fv[i] = v[r];
+          S.fs[i] = sl;
+        } else {
+          file_direct(v[r], nd, sl);
+        }
+      }
+      pos += __popc(bal[r]);
+    }
+  }
   // CTA-collective, between chunks / loop iterations.
   __device__ __forceinline__ void chunk_end(PushSmem &S) {
     __syncthreads();
@@ -212,10 +267,9 @@ struct RelaxFn {
       if (nd[r] < dv[r]) low[r] = atomicMin(dist + v[r], nd[r]) > nd[r];
     }
 #pragma unroll
-    for (int r = 0; r < kU; r++) {
+    for (int r = 0; r < kU; r++)
       if (low[r]) relax++;
-      sink.append(S, low[r], v[r], (uint32_t)nd[r]);
-    }
+    sink.template append_n<kU>(S, low, v, (const uint32_t *)nd, nullptr);
   }
 };
 
