@@ -56,6 +56,8 @@ namespace {
 // then all bitmap loads, then the test-and-sets, then the winners' degrees.
 struct BfsPushFn {
   static constexpr int kWin = kU;  // windows per walk step
+  template <class Sink>
+  __device__ __forceinline__ void drain(Sink &, PushSmem &) {}  // nothing deferred
   const uint32_t *off;
   const int32_t *tgt;
   uint32_t *visited;

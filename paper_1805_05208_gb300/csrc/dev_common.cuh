@@ -468,6 +468,7 @@ __device__ __forceinline__ void walk_chunk(PushSmem &S, uint32_t m, uint32_t nv,
     }
     fn.batch(val, uu, idx, sink, S);
   }
+  fn.drain(sink, S);
 }
 
 // Blocked sparse edgeMap over the frontier `in` with chunks of B = 256 << s

@@ -134,6 +134,8 @@ struct TouchSink {
 // Push Update for kU windows: lanes visit[u] & ~seen[v] are OR-ed into next[v].
 struct MsPushFn {
   static constexpr int kWin = kU;  // windows per walk step
+  template <class Sink>
+  __device__ __forceinline__ void drain(Sink &, PushSmem &) {}  // nothing deferred
   const int32_t *tgt;
   const u64 *cur;
   const u64 *seen;

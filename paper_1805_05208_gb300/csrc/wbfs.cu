@@ -239,7 +239,10 @@ struct FileSink {
 };
 
 // Update of Alg. 3 for kU windows of arcs out of bucket b: all target and
-// weight loads, then the distance loads, then the writeMins.
+// weight loads, then the distance loads, then the writeMins.  The writeMins
+// of a step are consumed (successes filed) at the next step, after its
+// target loads are issued, so their latency overlaps the next step's loads;
+// drain() files the last step's.
 struct RelaxFn {
   static constexpr int kWin = kU;  // windows per walk step
   const int32_t *tgt;
@@ -247,29 +250,43 @@ struct RelaxFn {
   int32_t *dist;
   int32_t b;
   unsigned long long relax;
+  // the previous step: targets, proposed distances, writeMin results (equal
+  // to the proposal where no writeMin was issued)
+  int32_t pv[kU], pnd[kU], pold[kU];
+
+  template <class Sink>
+  __device__ __forceinline__ void drain(Sink &sink, PushSmem &S) {
+    bool low[kU];
+#pragma unroll
+    for (int r = 0; r < kU; r++) {
+      low[r] = pold[r] > pnd[r];
+      if (low[r]) relax++;
+    }
+    sink.template append_n<kU>(S, low, pv, (const uint32_t *)pnd, nullptr);
+#pragma unroll
+    for (int r = 0; r < kU; r++) pold[r] = pnd[r];
+  }
   template <class Sink>
   __device__ __forceinline__ void batch(const bool *val, const int32_t *, const uint32_t *idx,
                                         Sink &sink, PushSmem &S) {
-    int32_t v[kU], nd[kU], dv[kU];
+    int32_t v[kU], nd[kU];
 #pragma unroll
     for (int r = 0; r < kU; r++) {
       v[r] = val[r] ? __ldg(tgt + idx[r]) : 0;
       nd[r] = val[r] ? b + (int32_t)__ldg(w + idx[r]) : kInf;
     }
+    drain(sink, S);
     // read D at L2 (.cg): L1 lines of D go stale as other SMs lower it, and a
     // stale (larger) value only costs a writeMin that cannot succeed
+    int32_t dv[kU];
 #pragma unroll
     for (int r = 0; r < kU; r++) dv[r] = val[r] ? __ldcg(dist + v[r]) : kInf;
-    bool low[kU];
 #pragma unroll
     for (int r = 0; r < kU; r++) {
-      low[r] = false;
-      if (nd[r] < dv[r]) low[r] = atomicMin(dist + v[r], nd[r]) > nd[r];
+      pold[r] = nd[r] < dv[r] ? atomicMin(dist + v[r], nd[r]) : nd[r];
+      pv[r] = v[r];
+      pnd[r] = nd[r];
     }
-#pragma unroll
-    for (int r = 0; r < kU; r++)
-      if (low[r]) relax++;
-    sink.template append_n<kU>(S, low, v, (const uint32_t *)nd, nullptr);
   }
 };
 
