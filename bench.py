@@ -19,7 +19,6 @@ reference) on bounded samples of the same workload instead.
 from __future__ import annotations
 
 import argparse
-import glob
 import hashlib
 import json
 import os
@@ -167,13 +166,20 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def kernel_source_hash():
-    """Short hash of the CUDA sources (csrc/): a DRAM-traffic figure taken
-    with ncu is only reported while the kernels it measured are unchanged."""
+KERNEL_SOURCES = {
+    "bfs_kernel": ("bfs.cu", "dev_common.cuh", "gbf_impl.h"),
+    "wbfs_kernel": ("wbfs.cu", "dev_common.cuh", "gbf_impl.h"),
+    "msbfs_kernel": ("msbfs.cu", "dev_common.cuh", "gbf_impl.h"),
+}
+
+
+def kernel_source_hash(kernel):
+    """Short hash of the CUDA sources a kernel is built from: a DRAM-traffic
+    figure taken with ncu is only reported while those are unchanged."""
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1805_05208_gb300", "csrc", "*"))):
-        with open(p, "rb") as f:
-            h.update(os.path.basename(p).encode())
+    for name in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_1805_05208_gb300", "csrc", name), "rb") as f:
+            h.update(name.encode())
             h.update(f.read())
     return h.hexdigest()[:16]
 
@@ -188,7 +194,7 @@ def measured_traffic(workload, kernel):
     except (OSError, ValueError):
         return None
     e = table.get(workload)
-    if not e or e.get("kernel") != kernel or e.get("csrc_hash") != kernel_source_hash():
+    if not e or e.get("kernel") != kernel or e.get("csrc_hash") != kernel_source_hash(kernel):
         return None
     return e.get("bytes_per_launch")
 
@@ -370,7 +376,8 @@ def run_serve(args, wl, rank, world):
     rates = [int(r) for r in (args.rates.split(",") if args.rates else wl["rates"])]
     warm, meas = (args.serve_warm or wl["warm"]), (args.serve_meas or wl["meas"])
     modes = {
-        "batched": gb.gbf_server_options_default(bfs_engines=2, wbfs_engines=2, max_batch=64),
+        "batched": gb.gbf_server_options_default(bfs_engines=args.serve_engines[0],
+                                                 wbfs_engines=args.serve_engines[1], max_batch=64),
         "one_per_launch_fifo": gb.gbf_server_options_default(bfs_engines=1, wbfs_engines=1,
                                                              max_batch=1),
     }
@@ -538,7 +545,10 @@ def main():
     ap.add_argument("--rates", default="", help="serve: comma list of offered rates (q/s)")
     ap.add_argument("--serve-warm", type=int, default=0)
     ap.add_argument("--serve-meas", type=int, default=0)
+    ap.add_argument("--serve-engines", default="2,2",
+                    help="serve: BFS,wBFS engines of the batched server")
     args = ap.parse_args()
+    args.serve_engines = tuple(int(x) for x in args.serve_engines.split(","))
     args.warmup = max(args.warmup, 3)
     wl = WORKLOADS[args.workload]
 

@@ -230,8 +230,9 @@ gbf_status gbf_autotune(gbf_graph *g, int32_t kind, gbf_options *out);
  * the pending queue has room.  A dispatcher thread keeps engines busy, each
  * with its own stream and workspace: BFS engines coalesce up to max_batch
  * pending BFS queries of one graph into one 64-lane multi-source launch
- * (each lane writes its query's result slot); wBFS engines run one weighted
- * query each.  Engines run concurrently on equal shares of the GPU.
+ * (each lane writes its query's result slot), or run a batch smaller than
+ * min_batch as single-source launches; wBFS engines run one weighted query
+ * each.  Engines run concurrently on equal shares of the GPU.
  * Results stay on the device until polled.  The paper has no serving layer;
  * results are identical to the single-query calls.
  */
@@ -248,6 +249,9 @@ typedef struct {
   int32_t max_queue;     /* pending queries before submit returns GBF_ERR_BUSY (default 65536) */
   size_t hbm_budget;     /* device bytes for result slots (0 = a quarter of free HBM) */
   gbf_options kernel;    /* kernel knobs (ctas is capped to the engine's share) */
+  int32_t min_batch;     /* BFS batches with fewer queries run as single-source launches
+                            (default 8; a 64-lane launch costs about the same at any width) */
+  int32_t reserved;
 } gbf_server_options;
 
 typedef struct {

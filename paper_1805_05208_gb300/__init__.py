@@ -62,7 +62,8 @@ class gbf_stats(ctypes.Structure):
 class gbf_server_options(ctypes.Structure):
     _fields_ = [("bfs_engines", ctypes.c_int32), ("wbfs_engines", ctypes.c_int32),
                 ("max_batch", ctypes.c_int32), ("max_queue", ctypes.c_int32),
-                ("hbm_budget", ctypes.c_size_t), ("kernel", gbf_options)]
+                ("hbm_budget", ctypes.c_size_t), ("kernel", gbf_options),
+                ("min_batch", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class gbf_server_counters(ctypes.Structure):

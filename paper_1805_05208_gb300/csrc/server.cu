@@ -8,8 +8,10 @@
 //   - BFS engines take up to max_batch pending BFS requests of one graph
 //     (the graph whose oldest request is oldest) and run them as one 64-lane
 //     multi-source BFS launch whose lane i writes straight into request i's
-//     result slot; with max_batch = 1 they run the single-source BFS kernel
-//     instead (one query per launch);
+//     result slot.  A 64-lane launch costs about the same whatever the
+//     number of lanes in use, so a batch smaller than min_batch runs as
+//     single-source BFS launches back to back instead (and max_batch = 1
+//     gives one query per launch);
 //   - wBFS engines take the oldest weighted request.
 // Engines run concurrently; each persistent launch gets an equal share of
 // the GPU's resident CTAs, so all engines' CTAs can be co-resident at once.
@@ -66,7 +68,7 @@ struct Engine {
 struct gbf_server {
   std::vector<gbf::Graph *> graphs;
   gbf_server_options opt;
-  gbf::Opts kopt_bfs, kopt_wbfs;
+  gbf::Opts kopt_bfs, kopt_single, kopt_wbfs;
   int32_t max_n = 0;
   char *slot_mem = nullptr;
   size_t slot_bytes = 0;
@@ -146,8 +148,14 @@ void dispatch(gbf_server *s, Engine *e) {
   e->graph = best;
   Graph &g = *s->graphs[best];
   gbf_status st;
-  if (kmax == 1) st = launch_bfs(g, e->ws, srcs[0], rows[0], nullptr, s->kopt_bfs, e->st);
-  else st = launch_msbfs_rows(g, e->ws, srcs, (int32_t)e->batch.size(), rows, s->kopt_bfs, e->st);
+  const int k = (int)e->batch.size();
+  if (kmax == 1 || k < s->opt.min_batch) {
+    st = GBF_OK;
+    for (int i = 0; i < k && st == GBF_OK; i++)
+      st = launch_bfs(g, e->ws, srcs[i], rows[i], nullptr, s->kopt_single, e->st);
+  } else {
+    st = launch_msbfs_rows(g, e->ws, srcs, (int32_t)k, rows, s->kopt_bfs, e->st);
+  }
   if (st != GBF_OK) {
     for (uint64_t t : e->batch) {
       Request &r = s->reqs[t];
@@ -232,6 +240,7 @@ gbf_status gbf_server_options_default(gbf_server_options *o) {
   o->bfs_engines = 2;
   o->wbfs_engines = 2;
   o->max_batch = 64;
+  o->min_batch = 8;
   o->max_queue = 1 << 16;
   o->hbm_budget = 0;
   gbf_options_default(&o->kernel);
@@ -252,6 +261,7 @@ gbf_status gbf_server_create(gbf_graph *const *graphs, int32_t ngraphs,
   }
   s->opt.max_batch = std::max(1, std::min(64, s->opt.max_batch ? s->opt.max_batch : 64));
   if (s->opt.max_queue <= 0) s->opt.max_queue = 1 << 16;
+  s->opt.min_batch = std::max(0, std::min(65, s->opt.min_batch));
   uint32_t max_m = 0, max_w = 0;
   bool any_w = false;
   for (int i = 0; i < ngraphs; i++) {
@@ -318,10 +328,11 @@ gbf_status gbf_server_create(gbf_graph *const *graphs, int32_t ngraphs,
   // engines' persistent launches are co-resident whatever runs together
   gbf_options ko = s->opt.kernel;
   s->kopt_bfs = resolve(&ko, *s->graphs[0], s->opt.max_batch > 1 ? GBF_TUNE_MSBFS : GBF_TUNE_BFS);
+  s->kopt_single = resolve(&ko, *s->graphs[0], GBF_TUNE_BFS);
   s->kopt_wbfs = resolve(&ko, *s->graphs[0], GBF_TUNE_WBFS);
   {
-    int per_sm = s->opt.max_batch > 1 ? resident_ctas_per_sm_msbfs(s->kopt_bfs)
-                                      : resident_ctas_per_sm_bfs(s->kopt_bfs);
+    int per_sm = resident_ctas_per_sm_bfs(s->kopt_single);
+    if (s->opt.max_batch > 1) per_sm = std::min(per_sm, resident_ctas_per_sm_msbfs(s->kopt_bfs));
     if (any_w && s->opt.wbfs_engines > 0) {
       const int nB = (int)std::min<uint32_t>(std::max<uint32_t>(max_w + 1, 2), 256);
       per_sm = std::min(per_sm, resident_ctas_per_sm_wbfs(s->kopt_wbfs, nB));
@@ -329,6 +340,7 @@ gbf_status gbf_server_create(gbf_graph *const *graphs, int32_t ngraphs,
     if (per_sm < 1) return fail((set_error("kernels do not fit on an SM"), GBF_ERR_INVALID));
     const int share = std::max(1, (sms * per_sm) / nengines);
     if (s->kopt_bfs.ctas == 0 || s->kopt_bfs.ctas > share) s->kopt_bfs.ctas = share;
+    if (s->kopt_single.ctas == 0 || s->kopt_single.ctas > share) s->kopt_single.ctas = share;
     if (s->kopt_wbfs.ctas == 0 || s->kopt_wbfs.ctas > share) s->kopt_wbfs.ctas = share;
   }
   s->worker = std::thread(worker_loop, s);
