@@ -253,6 +253,7 @@ struct RelaxFn {
   // the previous step: targets, proposed distances, writeMin results (equal
   // to the proposal where no writeMin was issued)
   int32_t pv[kU], pnd[kU], pold[kU];
+  uint64_t stream_pol, keep_pol;  // L2 policies: arcs leave first, D stays
 
   template <class Sink>
   __device__ __forceinline__ void drain(Sink &sink, PushSmem &S) {
@@ -272,15 +273,15 @@ struct RelaxFn {
     int32_t v[kU], nd[kU];
 #pragma unroll
     for (int r = 0; r < kU; r++) {
-      v[r] = val[r] ? __ldg(tgt + idx[r]) : 0;
-      nd[r] = val[r] ? b + (int32_t)__ldg(w + idx[r]) : kInf;
+      v[r] = val[r] ? (int32_t)ldg_pol(tgt + idx[r], stream_pol) : 0;
+      nd[r] = val[r] ? b + (int32_t)ldg_pol(w + idx[r], stream_pol) : kInf;
     }
     drain(sink, S);
     // read D at L2 (.cg): L1 lines of D go stale as other SMs lower it, and a
     // stale (larger) value only costs a writeMin that cannot succeed
     int32_t dv[kU];
 #pragma unroll
-    for (int r = 0; r < kU; r++) dv[r] = val[r] ? __ldcg(dist + v[r]) : kInf;
+    for (int r = 0; r < kU; r++) dv[r] = val[r] ? (int32_t)ldcg_pol(dist + v[r], keep_pol) : kInf;
 #pragma unroll
     for (int r = 0; r < kU; r++) {
       pold[r] = nd[r] < dv[r] ? atomicMin(dist + v[r], nd[r]) : nd[r];
@@ -485,6 +486,8 @@ __global__ void __launch_bounds__(1024) wbfs_kernel(WbfsParams P) {
     // ---------------- edgeMapData over the live entries of bucket b
     QueueOut fout{P.q, P.qoff, nullptr, P.cs, fctr, (uint32_t)g.n, P.cs_cap};
     RelaxFn fn{g.tgt, g.w, P.dist, b, 0};
+    fn.stream_pol = l2_evict_first();
+    fn.keep_pol = l2_evict_last();
     const int32_t *sl = P.slots + (size_t)sb * (size_t)g.n;
     for (uint32_t it = blockIdx.x * blockDim.x; it < cntb; it += gs) {
       const uint32_t i = it + threadIdx.x;
