@@ -1,0 +1,55 @@
+"""CPU tests of bench.py's host logic: the byte model, the traversed-edge
+count, the traffic lookup keyed by the kernel's own sources, and the
+multi-rank reduction (covered in test_multirank_cpu.py)."""
+import json
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+import graphgen as G  # noqa: E402
+
+
+def test_traversed_edges_counts_reached_component():
+    csr = G.csr_from_edges(6, [(0, 1), (1, 2), (3, 4)])
+    dist = np.array([0, 1, 2, bench.INF, bench.INF, bench.INF], dtype=np.int64)
+    # reached {0, 1, 2}: degrees 1 + 2 + 1 = 4 arcs = 2 undirected edges
+    assert bench.traversed_edges(csr, dist) == 2
+
+
+def test_bytes_model_terms():
+    st = dict(edges_scanned=10, vertices_expanded=3, relaxations=4, bucket_inserts=5,
+              vertices_reached=6, pull_rounds=1, heavy_vertices=2)
+    n = 64
+    assert bench.bytes_model("wbfs", n, st) == 4 * n + 16 * 5 + 12 * 10 + 8 * 4 + 16 * 2
+    assert bench.bytes_model("bfs", n, st) == 8 * n + n // 8 + 12 * 3 + 8 * 10 + 24 * 6 + 3 * (n // 8)
+
+
+def test_kernel_source_hash_tracks_only_its_sources():
+    h = {k: bench.kernel_source_hash(k) for k in bench.KERNEL_SOURCES}
+    assert len(set(h.values())) == len(h)          # different file sets
+    assert all(len(v) == 16 for v in h.values())
+    assert h == {k: bench.kernel_source_hash(k) for k in bench.KERNEL_SOURCES}  # stable
+
+
+def test_measured_traffic_needs_matching_sources(tmp_path, monkeypatch):
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "traffic.json").write_text(json.dumps({
+        "w": {"kernel": "wbfs_kernel", "csrc_hash": bench.kernel_source_hash("wbfs_kernel"),
+              "bytes_per_launch": 123},
+        "b": {"kernel": "bfs_kernel", "csrc_hash": "0" * 16, "bytes_per_launch": 456}}))
+    csrc = tmp_path / "paper_1805_05208_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    for name in {n for v in bench.KERNEL_SOURCES.values() for n in v}:
+        with open(os.path.join(ROOT, "paper_1805_05208_gb300", "csrc", name), "rb") as f:
+            (csrc / name).write_bytes(f.read())
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.measured_traffic("w", "wbfs_kernel") == 123
+    assert bench.measured_traffic("w", "bfs_kernel") is None      # other kernel
+    assert bench.measured_traffic("b", "bfs_kernel") is None      # sources changed since
+    assert bench.measured_traffic("missing", "bfs_kernel") is None

@@ -49,11 +49,15 @@ def _expected(csr, kind, s):
     return oracle.bfs(csr, s, parents=False)[0] if kind == 0 else oracle.dijkstra(csr, s)
 
 
-@pytest.mark.parametrize("max_batch", [64, 1])
-def test_served_equals_alone(gb, graphs, max_batch):
+@pytest.mark.parametrize("max_batch,min_batch", [(64, 8), (1, 8), (64, 0), (64, 65)])
+def test_served_equals_alone(gb, graphs, max_batch, min_batch):
+    """min_batch 0: every batch runs as one 64-lane launch; 65: every batch
+    runs as single-source launches; 8: small batches single, large ones
+    packed."""
     hs = [gb.Graph(c) for c in graphs]
     srv = gb.gbf_server_create([h.h for h in hs],
                                gb.gbf_server_options_default(max_batch=max_batch,
+                                                             min_batch=min_batch,
                                                              hbm_budget=64 << 20))
     rng = np.random.default_rng(7)
     queries = {}

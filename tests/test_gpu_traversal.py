@@ -99,6 +99,23 @@ def test_bfs_config_rmat16_max_degree_source(gb):
     assert st["device_error"] == 0
 
 
+def test_bfs_repeated_block1024_conversions(gb):
+    """Block 1024 with dense levels followed by sparse ones (bitmap -> queue
+    conversions) and one CTA doing most of a dense level, repeated: this
+    caught warps disagreeing on whether to flush the shared staging area."""
+    csr = G.rmat(13, 16, seed=13)
+    srcs = list(G.sources(csr, 4, seed=3)) + [G.max_degree_vertex(csr)]
+    refs = {int(s): oracle.bfs(csr, int(s), parents=False)[0] for s in srcs}
+    g = gb.Graph(csr)
+    for blk, hc in ((1024, 0), (1024, 4096), (512, 0)):
+        opt = gb.gbf_options_default(block=blk, heavy_cutoff=hc)
+        for _ in range(20):
+            for s in srcs:
+                d, _ = g.bfs(int(s), opt=opt)
+                assert np.array_equal(d, refs[int(s)]), (blk, hc, int(s))
+    g.close()
+
+
 def test_bfs_grid_deleted_edges(gb):
     csr = G.grid(200, 300, 0.1, seed=7)
     _bfs_parity(gb, csr, [0, 123, 59999], opts=(None, gb.gbf_options_default(ctas=3)))
