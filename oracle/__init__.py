@@ -1,9 +1,10 @@
 """The oracle — TEST INFRASTRUCTURE, not part of the product.
 
 A plain serial CPU statement of what the traversal path computes, written
-from the paper's problem statements (§4, "Breadth-First Search" and
-"Integral-Weight SSSP"): hop distances and shortest-path distances, each the
-unique answer to its definition.  ``oracle.c`` holds the arithmetic (FIFO
+from the paper's problem statements (§4, "Breadth-First Search",
+"Integral-Weight SSSP", "General-Weight SSSP (Bellman-Ford)", "Widest
+Path"): hop distances, shortest-path distances and widest-path widths, each
+the unique answer to its definition.  ``oracle.c`` holds the arithmetic (FIFO
 BFS, binary-heap Dijkstra, Floyd–Warshall, output validators); this module
 only marshals numpy arrays into it.
 
@@ -58,6 +59,9 @@ def _load():
             lib.or_bfs.restype = ctypes.c_int64
             lib.or_dijkstra.argtypes = [ctypes.c_int32, P, P, P, ctypes.c_int32, P]
             lib.or_dijkstra.restype = ctypes.c_int64
+            lib.or_bellman_ford.argtypes = [ctypes.c_int32, P, P, P, ctypes.c_int32, ctypes.c_int,
+                                            P]
+            lib.or_bellman_ford.restype = ctypes.c_int64
             lib.or_floyd_warshall.argtypes = [ctypes.c_int32, P, P, P, P]
             lib.or_floyd_warshall.restype = ctypes.c_int
             lib.or_check_bfs.argtypes = [ctypes.c_int32, P, P, ctypes.c_int32, P, P,
@@ -107,6 +111,38 @@ def dijkstra(g, src: int, w=None):
     if rc < 0:
         raise ValueError("or_dijkstra: bad argument")
     return dist
+
+
+def _bellman_ford(g, src: int, mode: int):
+    lib = _load()
+    if g.w is None:
+        raise ValueError("graph has no weights")
+    off, po = _c(g.off, np.uint32)
+    tgt = np.ascontiguousarray(g.tgt, dtype=np.int32) if g.m else np.zeros(1, np.int32)
+    ww = np.ascontiguousarray(g.w, dtype=np.uint32) if g.m else np.zeros(1, np.uint32)
+    out = np.empty(g.n, dtype=np.int32)
+    rc = lib.or_bellman_ford(g.n, po, tgt.ctypes.data, ww.ctypes.data, int(src), mode,
+                             out.ctypes.data)
+    if rc == -2:
+        raise OverflowError("distance exceeds int32")
+    if rc < 0:
+        raise ValueError("or_bellman_ford: bad argument")
+    return out, int(rc)
+
+
+def bellman_ford(g, src: int, rounds: bool = False):
+    """General-weight SSSP by frontier Bellman-Ford rounds (Alg. 4): int32
+    distances, INF if unreachable; with rounds=True also the round count."""
+    d, r = _bellman_ford(g, src, 0)
+    return (d, r) if rounds else d
+
+
+def widest_path(g, src: int, rounds: bool = False):
+    """Single-source widest path: for each v the largest, over paths from src,
+    smallest weight on the path; INF at the source (empty path) and, by the
+    paper's output convention, at unreachable vertices."""
+    d, r = _bellman_ford(g, src, 1)
+    return (d, r) if rounds else d
 
 
 def floyd_warshall(g, weighted: bool):

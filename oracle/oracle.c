@@ -11,7 +11,12 @@
  *     positive integer edge weights, "infinity" if unreachable.
  * Both results are unique, so the oracle computes the plain definitions —
  * a FIFO-queue BFS and a binary-heap Dijkstra — with no frontier or bucket
- * machinery.  Floyd–Warshall is included as a brute-force check for tiny
+ * machinery.
+ *   - General-weight SSSP by Bellman-Ford (Alg. 4) and single-source widest
+ *     path (the same rounds over the (max, min) semiring, §5 "Widest Path"):
+ *     these follow the algorithm's rounds in order (frontier, Update with a
+ *     flag per vertex, ResetFlags), since their answers are pinned by other
+ *     methods (Dijkstra, Floyd–Warshall, maximum spanning trees).  Floyd–Warshall is included as a brute-force check for tiny
  * graphs.  Infinity is INT32_MAX; unreachable parents are -1; the parent of
  * the source is the source itself.
  *
@@ -139,6 +144,77 @@ int64_t or_dijkstra(int32_t n, const uint32_t *off, const int32_t *tgt, const ui
   free(d);
   free(h);
   free(done);
+  return rc;
+}
+
+/* ------------------------------------------------ Bellman-Ford (Alg. 4) */
+/* Frontier rounds: every frontier vertex s relaxes its arcs (s, d, w) in CSR
+ * order; a d whose value improved joins the next frontier once (its flag);
+ * the flags of the new frontier are then reset.  mode 0: D = min over paths
+ * of the weight sum ((min, +)), D[src] = 0, unreachable = infinity.  mode 1:
+ * widest path ((max, min)): D[v] = max over paths of the smallest weight on
+ * the path; the empty path at the source has width infinity, and internally
+ * 0 means "no path yet" (weights are >= 1).  The paper's output convention
+ * gives unreachable vertices infinity as well.  Returns the number of rounds,
+ * -1 on a bad argument, -2 if a sum exceeds int32 (mode 0). */
+int64_t or_bellman_ford(int32_t n, const uint32_t *off, const int32_t *tgt, const uint32_t *w,
+                        int32_t src, int mode, int32_t *out) {
+  if (n <= 0 || src < 0 || src >= n || !w || (mode != 0 && mode != 1)) return -1;
+  int64_t *D = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+  char *fl = (char *)calloc((size_t)n, 1);
+  int32_t *F = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+  int32_t *F2 = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+  if (!D || !fl || !F || !F2) {
+    free(D);
+    free(fl);
+    free(F);
+    free(F2);
+    return -1;
+  }
+  const int64_t unset = mode == 0 ? INT64_MAX : 0;
+  for (int32_t v = 0; v < n; v++) D[v] = unset;
+  D[src] = mode == 0 ? 0 : INT64_MAX;
+  int64_t nf = 1, rounds = 0;
+  F[0] = src;
+  while (nf > 0 && rounds < (int64_t)n) {
+    int64_t nf2 = 0;
+    for (int64_t i = 0; i < nf; i++) {
+      const int32_t s = F[i];
+      for (uint32_t k = off[s]; k < off[s + 1]; k++) {
+        const int32_t d = tgt[k];
+        const int64_t c = mode == 0 ? D[s] + (int64_t)w[k]
+                                    : (D[s] < (int64_t)w[k] ? D[s] : (int64_t)w[k]);
+        const int better = mode == 0 ? c < D[d] : c > D[d];
+        if (better) {
+          D[d] = c;
+          if (!fl[d]) {
+            fl[d] = 1;
+            F2[nf2++] = d;
+          }
+        }
+      }
+    }
+    for (int64_t i = 0; i < nf2; i++) fl[F2[i]] = 0; /* ResetFlags over the new frontier */
+    int32_t *t = F;
+    F = F2;
+    F2 = t;
+    nf = nf2;
+    rounds++;
+  }
+  int64_t rc = rounds;
+  for (int32_t v = 0; v < n; v++) {
+    if (mode == 0) {
+      if (D[v] == INT64_MAX) out[v] = OR_INF;
+      else if (D[v] >= OR_INF) { out[v] = OR_INF; rc = -2; }
+      else out[v] = (int32_t)D[v];
+    } else {
+      out[v] = (D[v] == 0 || D[v] >= OR_INF) ? OR_INF : (int32_t)D[v];
+    }
+  }
+  free(D);
+  free(fl);
+  free(F);
+  free(F2);
   return rc;
 }
 
