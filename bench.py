@@ -48,6 +48,11 @@ WORKLOADS = {
                        desc="BFS (dist+parent), RMAT scale 22 ef16, 8 seeded sources"),
     "bfs-rmat26": dict(kind="bfs", graph="rmat", scale=26, ef=16, w=None, nsrc=4,
                        desc="BFS (dist+parent), RMAT scale 26 ef16 (~2.1B arcs), 4 seeded sources"),
+    "bf-rmat22": dict(kind="bf", graph="rmat", scale=22, ef=16, w=(1, 22), nsrc=8,
+                      desc="Bellman-Ford (Alg. 4), RMAT scale 22 ef16, w in [1,22), 8 seeded sources"),
+    "widest-rmat22": dict(kind="widest", graph="rmat", scale=22, ef=16, w=(1, 22), nsrc=8,
+                          desc="widest path ((max,min) Bellman-Ford rounds), RMAT scale 22 ef16, "
+                               "w in [1,22), 8 seeded sources"),
     "wbfs-rmat26": dict(kind="wbfs", graph="rmat", scale=26, ef=16, w=(1, 22), nsrc=2,
                         desc="wBFS, RMAT scale 26 ef16, w in [1,22), 2 seeded sources"),
     "msbfs-rmat24": dict(kind="msbfs", graph="rmat", scale=24, ef=16, w=None, nsrc=64,
@@ -104,6 +109,22 @@ def make_sources(g, wl, rank=0):
             s[0] = 0
         return s
     return G.sources(g, k, seed=3 + 1000 * rank)
+
+
+ORACLE_NAME = {"bfs": "FIFO BFS", "wbfs": "binary-heap Dijkstra",
+               "bf": "frontier Bellman-Ford", "widest": "(max,min) Bellman-Ford rounds"}
+
+
+def reach_of(kind, g, src, out):
+    """Values whose finite entries mark the source's component.  Widest path
+    gives unreachable vertices INF, like the source itself, so its component
+    is every vertex with a finite width plus the source."""
+    d = out.cpu().numpy() if hasattr(out, "cpu") else out
+    if kind != "widest":
+        return d
+    reach = np.where(d != INF, 0, INF).astype(np.int64)
+    reach[src] = 0
+    return reach
 
 
 def traversed_edges(g, dist):
@@ -210,6 +231,12 @@ def bytes_model(kind, n, st):
         # and the bucket write (8); per heavy vertex: queue + degree prefix
         # written and read (16)
         return 4 * n + 16 * I + 12 * E + 8 * R + 16 * st["heavy_vertices"]
+    if kind in ("bf", "widest"):
+        # init values (4n) and both flag bitmaps (n/4); per frontier vertex:
+        # queue, degree prefix, first arc, flag reset (16); per scanned arc:
+        # target, weight, source value, target value (16); per successful
+        # writeMin/Max: the atomic and the flag test-and-set (8)
+        return 4 * n + n // 4 + 16 * V + 16 * E + 8 * R
     if kind == "msbfs":
         # init seen/visit/next (32n); every dist[i][v] written once (4kn); per
         # scanned arc: target + the neighbour's lane word (12); per frontier
@@ -249,6 +276,13 @@ def cpu_reference_sample(g, wl, srcs, budget_s=15.0, max_queries=None):
         t0 = time.perf_counter()
         if wl["kind"] == "wbfs":
             d = oracle.dijkstra(g, int(s))
+        elif wl["kind"] == "bf":
+            d = oracle.bellman_ford(g, int(s))
+        elif wl["kind"] == "widest":
+            # the widest-path output marks unreachable vertices INF too: count
+            # the source's component by hops
+            oracle.widest_path(g, int(s))
+            d, _ = oracle.bfs(g, int(s), parents=False)
         else:
             d, _ = oracle.bfs(g, int(s))
         t += time.perf_counter() - t0
@@ -592,6 +626,10 @@ def main():
     def launch(i):
         if kind == "wbfs":
             gb.gbf_wbfs(graph.h, int(srcs[i]), outs[i], opt, stream)
+        elif kind == "bf":
+            gb.gbf_bellman_ford(graph.h, int(srcs[i]), outs[i], opt, stream)
+        elif kind == "widest":
+            gb.gbf_widest_path(graph.h, int(srcs[i]), outs[i], opt, stream)
         else:
             gb.gbf_bfs(graph.h, int(srcs[i]), outs[i], pars[i], opt, stream)
 
@@ -602,7 +640,7 @@ def main():
             launch(i)
             if w == 0:
                 stats.append(gb.gbf_wait(graph.h, stream))
-                te.append(traversed_edges(g, outs[i].cpu().numpy()))
+                te.append(traversed_edges(g, reach_of(kind, g, int(srcs[i]), outs[i])))
                 if i == 0:
                     trace0 = gb.gbf_trace(graph.h)
     gb.gbf_wait(graph.h, stream)
@@ -656,6 +694,10 @@ def main():
         for i in range(len(srcs)):
             if kind == "wbfs":
                 gb.gbf_wbfs(graph.h, int(srcs[i]), host_out[i], opt, None)
+            elif kind == "bf":
+                gb.gbf_bellman_ford(graph.h, int(srcs[i]), host_out[i], opt, None)
+            elif kind == "widest":
+                gb.gbf_widest_path(graph.h, int(srcs[i]), host_out[i], opt, None)
             else:
                 gb.gbf_bfs(graph.h, int(srcs[i]), host_out[i], host_par[i], opt, None)
     e2e_s = time.perf_counter() - t0
@@ -673,7 +715,7 @@ def main():
             te_c, t_c, q = cpu_reference_sample(g, wl, srcs, budget_s=args.cpu_budget)
             cpu = {"value": te_c / t_c / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
                    "sample": f"{q} of the {len(srcs)} queries of one step, serial oracle "
-                             f"({'binary-heap Dijkstra' if kind == 'wbfs' else 'FIFO BFS'}), "
+                             f"({ORACLE_NAME[kind]}), "
                              f"{t_c:.1f} s"}
         clocks = clk.summary()
         line = {

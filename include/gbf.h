@@ -184,8 +184,34 @@ gbf_status gbf_wbfs(gbf_graph *g, int32_t src, int32_t *dist, int mem, const gbf
                     void *cuda_stream);
 
 /*
+ * gbf_bellman_ford — general-weight single-source shortest paths by the
+ * frontier Bellman-Ford of §4 "General-Weight SSSP (Bellman-Ford)" (Alg. 4):
+ * rounds of the blocked sparse edgeMap whose Update relaxes D[s] + w with
+ * writeMin and puts an improved target on the next frontier once (a
+ * test-and-set flag, reset a round later).  Weights are the graph's uint32
+ * weights (>= 1, so a symmetric graph has no negative cycle).
+ *   dist    int32[n]: shortest-path distance, GBF_INF if unreachable
+ *   mem     GBF_HOST: blocks; GBF_DEVICE: stream-ordered, see gbf_wait
+ * Errors: as gbf_wbfs.  The sparse (push) direction only.
+ */
+gbf_status gbf_bellman_ford(gbf_graph *g, int32_t src, int32_t *dist, int mem,
+                            const gbf_options *opt, void *cuda_stream);
+
+/*
+ * gbf_widest_path — single-source widest (bottleneck) path (§4 "Widest
+ * Path"; §5: the Bellman-Ford rounds of Alg. 4 over the (max, min) semiring):
+ * width[v] is the largest, over paths from src to v, of the smallest weight
+ * on the path.  width[src] = GBF_INF (the empty path) and, following the
+ * problem statement's output convention, width[v] = GBF_INF for unreachable v.
+ * Arguments and errors as gbf_bellman_ford.
+ */
+gbf_status gbf_widest_path(gbf_graph *g, int32_t src, int32_t *width, int mem,
+                           const gbf_options *opt, void *cuda_stream);
+
+/*
  * gbf_wait — synchronise `cuda_stream` and return the device-side status of
- * the last gbf_bfs / gbf_wbfs / gbf_msbfs issued on g with GBF_DEVICE
+ * the last gbf_bfs / gbf_wbfs / gbf_msbfs / gbf_bellman_ford /
+ * gbf_widest_path issued on g with GBF_DEVICE
  * buffers; fills *stats if non-NULL.
  */
 gbf_status gbf_wait(gbf_graph *g, void *cuda_stream, gbf_stats *stats);

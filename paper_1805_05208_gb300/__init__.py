@@ -100,6 +100,8 @@ def _load() -> ctypes.CDLL:
         "gbf_graph_device_bytes": (S, [P, ctypes.POINTER(ctypes.c_size_t)]),
         "gbf_bfs": (S, [P, I32, P, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
         "gbf_wbfs": (S, [P, I32, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
+        "gbf_bellman_ford": (S, [P, I32, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
+        "gbf_widest_path": (S, [P, I32, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
         "gbf_wait": (S, [P, P, ctypes.POINTER(gbf_stats)]),
         "gbf_msbfs": (S, [P, P, I32, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
         "gbf_server_options_default": (S, [ctypes.POINTER(gbf_server_options)]),
@@ -220,6 +222,22 @@ def gbf_wbfs(h: int, src: int, dist, opt: Optional[gbf_options] = None, stream=N
     """Integral-weight SSSP from src into dist."""
     pd, mem = _ptr(dist)
     _check(_lib.gbf_wbfs(h, int(src), pd, mem, _opt(opt), _stream(stream)), "gbf_wbfs")
+
+
+def gbf_bellman_ford(h: int, src: int, dist, opt: Optional[gbf_options] = None,
+                     stream=None) -> None:
+    """General-weight SSSP from src by frontier Bellman-Ford rounds into dist."""
+    pd, mem = _ptr(dist)
+    _check(_lib.gbf_bellman_ford(h, int(src), pd, mem, _opt(opt), _stream(stream)),
+           "gbf_bellman_ford")
+
+
+def gbf_widest_path(h: int, src: int, width, opt: Optional[gbf_options] = None,
+                    stream=None) -> None:
+    """Single-source widest (bottleneck) path widths from src into width."""
+    pd, mem = _ptr(width)
+    _check(_lib.gbf_widest_path(h, int(src), pd, mem, _opt(opt), _stream(stream)),
+           "gbf_widest_path")
 
 
 def gbf_msbfs(h: int, srcs, dist, opt: Optional[gbf_options] = None, stream=None) -> None:
@@ -375,6 +393,16 @@ class Graph:
     def wbfs(self, src: int, opt=None):
         d = np.empty(self.n, dtype=np.int32)
         gbf_wbfs(self.h, src, d, opt)
+        return d
+
+    def bellman_ford(self, src: int, opt=None):
+        d = np.empty(self.n, dtype=np.int32)
+        gbf_bellman_ford(self.h, src, d, opt)
+        return d
+
+    def widest_path(self, src: int, opt=None):
+        d = np.empty(self.n, dtype=np.int32)
+        gbf_widest_path(self.h, src, d, opt)
         return d
 
     def stats(self, stream=None) -> dict:

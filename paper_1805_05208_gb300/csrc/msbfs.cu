@@ -87,20 +87,6 @@ struct TouchSink {
   unsigned int *count;
   uint32_t cap;
   Ctl *ctl;
-  __device__ __forceinline__ void append(PushSmem &, bool emit, int32_t v, uint32_t) {
-    const unsigned bal = __ballot_sync(kFull, emit);
-    if (bal == 0) return;
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(bal) - 1;
-    uint32_t pos = 0;
-    if (lane == leader) pos = atomicAdd(count, (unsigned)__popc(bal));
-    pos = __shfl_sync(kFull, pos, leader);
-    if (emit) {
-      const uint32_t r = pos + __popc(bal & lanemask_lt());
-      if (r < cap) list[r] = v;
-      else raise_error(ctl, GBF_ERR_OVERFLOW, 10);
-    }
-  }
   // Warp-collective: the U appends of one walk step with one atomic.
   template <int U>
   __device__ __forceinline__ void append_n(PushSmem &, const bool *emit, const int32_t *v,
@@ -160,7 +146,6 @@ struct MsPushFn {
       first[r] = false;
       if (m) first[r] = atomicOr(next + v[r], m) == 0ull;
     }
-#pragma unroll
     sink.template append_n<kU>(S, first, v, nullptr, nullptr);
   }
 };
