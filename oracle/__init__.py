@@ -3,8 +3,9 @@
 A plain serial CPU statement of what the traversal path computes, written
 from the paper's problem statements (§4, "Breadth-First Search",
 "Integral-Weight SSSP", "General-Weight SSSP (Bellman-Ford)", "Widest
-Path"): hop distances, shortest-path distances and widest-path widths, each
-the unique answer to its definition.  ``oracle.c`` holds the arithmetic (FIFO
+Path", "Single-Source Betweenness Centrality"): hop distances,
+shortest-path distances, widest-path widths and betweenness dependencies,
+each the unique answer to its definition.  ``oracle.c`` holds the arithmetic (FIFO
 BFS, binary-heap Dijkstra, Floyd–Warshall, output validators); this module
 only marshals numpy arrays into it.
 
@@ -62,6 +63,8 @@ def _load():
             lib.or_bellman_ford.argtypes = [ctypes.c_int32, P, P, P, ctypes.c_int32, ctypes.c_int,
                                             P]
             lib.or_bellman_ford.restype = ctypes.c_int64
+            lib.or_betweenness.argtypes = [ctypes.c_int32, P, P, ctypes.c_int32, P, P, P]
+            lib.or_betweenness.restype = ctypes.c_int64
             lib.or_floyd_warshall.argtypes = [ctypes.c_int32, P, P, P, P]
             lib.or_floyd_warshall.restype = ctypes.c_int
             lib.or_check_bfs.argtypes = [ctypes.c_int32, P, P, ctypes.c_int32, P, P,
@@ -143,6 +146,22 @@ def widest_path(g, src: int, rounds: bool = False):
     paper's output convention, at unreachable vertices."""
     d, r = _bellman_ford(g, src, 1)
     return (d, r) if rounds else d
+
+
+def betweenness(g, src: int, full: bool = False):
+    """Single-source betweenness dependencies (Alg. 2), fp64; with full=True
+    also the shortest-path counts and hop levels."""
+    lib = _load()
+    off, po = _c(g.off, np.uint32)
+    tgt = np.ascontiguousarray(g.tgt, dtype=np.int32) if g.m else np.zeros(1, np.int32)
+    D = np.empty(g.n, dtype=np.float64)
+    paths = np.empty(g.n, dtype=np.float64)
+    level = np.empty(g.n, dtype=np.int32)
+    rc = lib.or_betweenness(g.n, po, tgt.ctypes.data, int(src), D.ctypes.data,
+                            paths.ctypes.data, level.ctypes.data)
+    if rc < 0:
+        raise ValueError("or_betweenness: bad argument")
+    return (D, paths, level) if full else D
 
 
 def floyd_warshall(g, weighted: bool):

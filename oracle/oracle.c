@@ -16,7 +16,13 @@
  *     path (the same rounds over the (max, min) semiring, §5 "Widest Path"):
  *     these follow the algorithm's rounds in order (frontier, Update with a
  *     flag per vertex, ResetFlags), since their answers are pinned by other
- *     methods (Dijkstra, Floyd–Warshall, maximum spanning trees).  Floyd–Warshall is included as a brute-force check for tiny
+ *     methods (Dijkstra, Floyd–Warshall, maximum spanning trees).
+ *   - Single-source betweenness centrality (Alg. 2): a forward pass of
+ *     frontier rounds counting shortest paths (NumPaths, fetch-and-add) and
+ *     recording each round's frontier, then a backward pass over the
+ *     recorded frontiers in reverse accumulating dependencies, in fp64; it
+ *     is pinned against the definition (sums of path-count ratios over all
+ *     targets) computed by brute force.  Floyd–Warshall is included as a brute-force check for tiny
  * graphs.  Infinity is INT32_MAX; unreachable parents are -1; the parent of
  * the source is the source itself.
  *
@@ -216,6 +222,85 @@ int64_t or_bellman_ford(int32_t n, const uint32_t *off, const int32_t *tgt, cons
   free(F);
   free(F2);
   return rc;
+}
+
+/* ------------------------------------------- betweenness (Alg. 2) */
+/* Readings: NumPaths[r] = 1 and r is visited before the first round (the
+ * listing leaves the source's path count and flag at 0); NumPaths and the
+ * dependencies are fp64.  Forward: the frontier's vertices s add
+ * NumPaths[s] to every unvisited neighbour d (in CSR order); d joins the
+ * next frontier at its first contribution; the new frontier is recorded as a
+ * level and marked visited.  Backward: the levels in reverse; each level is
+ * marked visited, then every s in it adds NumPaths[d] / NumPaths[s] *
+ * (1 + D[s]) to each neighbour d not yet visited (the level above).
+ * Outputs: D (dependencies; 0 where unreachable), the path counts and the
+ * hop levels (-1 where unreachable) for the tests.  Returns the number of
+ * forward rounds, or -1 on a bad argument. */
+int64_t or_betweenness(int32_t n, const uint32_t *off, const int32_t *tgt, int32_t src,
+                       double *D, double *paths, int32_t *level) {
+  if (n <= 0 || src < 0 || src >= n) return -1;
+  char *vis = (char *)calloc((size_t)n, 1);
+  int32_t *order = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+  int64_t *lo = (int64_t *)malloc(sizeof(int64_t) * ((size_t)n + 2));
+  if (!vis || !order || !lo) {
+    free(vis);
+    free(order);
+    free(lo);
+    return -1;
+  }
+  for (int32_t v = 0; v < n; v++) {
+    D[v] = 0.0;
+    paths[v] = 0.0;
+    level[v] = -1;
+  }
+  paths[src] = 1.0;
+  vis[src] = 1;
+  level[src] = 0;
+  order[0] = src;
+  int64_t nl = 0, end = 1;  /* levels[k] = order[lo[k] .. lo[k+1]) */
+  lo[0] = 0;
+  lo[1] = 1;
+  int64_t fb = 0, fe = 1;   /* current frontier */
+  while (fe > fb) {
+    int64_t ne = end;
+    for (int64_t i = fb; i < fe; i++) {
+      const int32_t s = order[i];
+      for (uint32_t k = off[s]; k < off[s + 1]; k++) {
+        const int32_t d = tgt[k];
+        if (vis[d]) continue;
+        const double prev = paths[d];
+        paths[d] = prev + paths[s];
+        if (prev == 0.0) order[ne++] = d;
+      }
+    }
+    for (int64_t i = end; i < ne; i++) {
+      vis[order[i]] = 1;
+      level[order[i]] = (int32_t)(nl + 1);
+    }
+    nl++;
+    lo[nl + 1] = ne;
+    fb = end;
+    fe = ne;
+    end = ne;
+  }
+  /* lo[0..nl]: levels 0..nl-1 nonempty (the last recorded frontier is
+   * empty); backward over levels nl-1 .. 1 */
+  memset(vis, 0, (size_t)n);
+  for (int64_t L = nl - 1; L >= 1; L--) {
+    for (int64_t i = lo[L]; i < lo[L + 1]; i++) vis[order[i]] = 1;
+    for (int64_t i = lo[L]; i < lo[L + 1]; i++) {
+      const int32_t s = order[i];
+      for (uint32_t k = off[s]; k < off[s + 1]; k++) {
+        const int32_t d = tgt[k];
+        if (vis[d]) continue;
+        D[d] += paths[d] / paths[s] * (1.0 + D[s]);
+      }
+    }
+  }
+  free(vis);
+  free(order);
+  free(lo);
+  return nl;
 }
 
 /* --------------------------------------------------------- Floyd–Warshall */
