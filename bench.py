@@ -53,6 +53,9 @@ WORKLOADS = {
     "widest-rmat22": dict(kind="widest", graph="rmat", scale=22, ef=16, w=(1, 22), nsrc=8,
                           desc="widest path ((max,min) Bellman-Ford rounds), RMAT scale 22 ef16, "
                                "w in [1,22), 8 seeded sources"),
+    "bc-rmat22": dict(kind="bc", graph="rmat", scale=22, ef=16, w=None, nsrc=8,
+                      desc="single-source betweenness (Alg. 2, forward path counts + backward "
+                           "dependencies, fp64), RMAT scale 22 ef16, 8 seeded sources"),
     "wbfs-rmat26": dict(kind="wbfs", graph="rmat", scale=26, ef=16, w=(1, 22), nsrc=2,
                         desc="wBFS, RMAT scale 26 ef16, w in [1,22), 2 seeded sources"),
     "msbfs-rmat24": dict(kind="msbfs", graph="rmat", scale=24, ef=16, w=None, nsrc=64,
@@ -112,7 +115,8 @@ def make_sources(g, wl, rank=0):
 
 
 ORACLE_NAME = {"bfs": "FIFO BFS", "wbfs": "binary-heap Dijkstra",
-               "bf": "frontier Bellman-Ford", "widest": "(max,min) Bellman-Ford rounds"}
+               "bf": "frontier Bellman-Ford", "widest": "(max,min) Bellman-Ford rounds",
+               "bc": "betweenness forward + backward passes"}
 
 
 def reach_of(kind, g, src, out):
@@ -231,6 +235,12 @@ def bytes_model(kind, n, st):
         # and the bucket write (8); per heavy vertex: queue + degree prefix
         # written and read (16)
         return 4 * n + 16 * I + 12 * E + 8 * R + 16 * st["heavy_vertices"]
+    if kind == "bc":
+        # init path counts, dependencies (fp64) and levels (20n); per scanned
+        # arc in either pass: target, its level, one 8-byte value (16); per
+        # reached vertex: its queue entry written and read twice (24), path
+        # count and dependency (16)
+        return 20 * n + 16 * E + 40 * st["vertices_reached"]
     if kind in ("bf", "widest"):
         # init values (4n) and both flag bitmaps (n/4); per frontier vertex:
         # queue, degree prefix, first arc, flag reset (16); per scanned arc:
@@ -283,6 +293,9 @@ def cpu_reference_sample(g, wl, srcs, budget_s=15.0, max_queries=None):
             # the source's component by hops
             oracle.widest_path(g, int(s))
             d, _ = oracle.bfs(g, int(s), parents=False)
+        elif wl["kind"] == "bc":
+            _, _, lv = oracle.betweenness(g, int(s), full=True)
+            d = np.where(lv >= 0, lv, INF)
         else:
             d, _ = oracle.bfs(g, int(s))
         t += time.perf_counter() - t0
@@ -620,7 +633,8 @@ def main():
     kind = wl["kind"]
     if kind == "msbfs":
         return run_msbfs(args, wl, g, srcs, graph, opt, stream, dev, rank, world, barrier, dist_mod)
-    outs = [torch.empty(n, dtype=torch.int32, device=dev) for _ in srcs]
+    out_dtype = torch.float64 if kind == "bc" else torch.int32
+    outs = [torch.empty(n, dtype=out_dtype, device=dev) for _ in srcs]
     pars = [torch.empty(n, dtype=torch.int32, device=dev) for _ in srcs] if kind == "bfs" else None
 
     def launch(i):
@@ -630,6 +644,8 @@ def main():
             gb.gbf_bellman_ford(graph.h, int(srcs[i]), outs[i], opt, stream)
         elif kind == "widest":
             gb.gbf_widest_path(graph.h, int(srcs[i]), outs[i], opt, stream)
+        elif kind == "bc":
+            gb.gbf_betweenness(graph.h, int(srcs[i]), outs[i], opt, stream)
         else:
             gb.gbf_bfs(graph.h, int(srcs[i]), outs[i], pars[i], opt, stream)
 
@@ -640,7 +656,16 @@ def main():
             launch(i)
             if w == 0:
                 stats.append(gb.gbf_wait(graph.h, stream))
-                te.append(traversed_edges(g, reach_of(kind, g, int(srcs[i]), outs[i])))
+                if kind == "bc":
+                    # the component, from one untimed BFS of this library
+                    hops = torch.empty(n, dtype=torch.int32, device=dev)
+                    gb.gbf_bfs(graph.h, int(srcs[i]), hops, None, None, stream)
+                    gb.gbf_wait(graph.h, stream)
+                    te.append(traversed_edges(g, hops.cpu().numpy()))
+                    launch(i)
+                    stats[-1] = gb.gbf_wait(graph.h, stream)
+                else:
+                    te.append(traversed_edges(g, reach_of(kind, g, int(srcs[i]), outs[i])))
                 if i == 0:
                     trace0 = gb.gbf_trace(graph.h)
     gb.gbf_wait(graph.h, stream)
@@ -683,7 +708,7 @@ def main():
     achieved = bytes_per_launch / (avg_launch_ms / 1e3) / 1e9
 
     # End to end: the C-ABI call with host buffers (D2H of each result inside).
-    host_out = [torch.empty(n, dtype=torch.int32, pin_memory=True).numpy() for _ in srcs]
+    host_out = [torch.empty(n, dtype=out_dtype, pin_memory=True).numpy() for _ in srcs]
     host_par = [torch.empty(n, dtype=torch.int32, pin_memory=True).numpy() for _ in srcs] \
         if kind == "bfs" else None
     e2e_steps = max(1, min(args.steps, 5))
@@ -698,6 +723,8 @@ def main():
                 gb.gbf_bellman_ford(graph.h, int(srcs[i]), host_out[i], opt, None)
             elif kind == "widest":
                 gb.gbf_widest_path(graph.h, int(srcs[i]), host_out[i], opt, None)
+            elif kind == "bc":
+                gb.gbf_betweenness(graph.h, int(srcs[i]), host_out[i], opt, None)
             else:
                 gb.gbf_bfs(graph.h, int(srcs[i]), host_out[i], host_par[i], opt, None)
     e2e_s = time.perf_counter() - t0
@@ -706,7 +733,7 @@ def main():
         dist_mod.all_reduce(t, op=dist_mod.ReduceOp.MAX)
         e2e_s = float(t.item())
     e2e_val = te_all * e2e_steps / e2e_s / 1e9
-    d2h = len(srcs) * n * 4 * (2 if kind == "bfs" else 1)
+    d2h = len(srcs) * n * (8 if kind == "bc" else 4 * (2 if kind == "bfs" else 1))
 
     line = None
     if rank == 0:
@@ -721,7 +748,8 @@ def main():
         line = {
             "metric": "GTEPS", "value": value, "unit": "GTEPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if kind == "bc" else "int32",
             "data": "synthetic",
             "config": {"workload": args.workload, "desc": wl["desc"], "n": n, "arcs": g.m,
                        "sources_per_step": len(srcs), "seeds": {"graph": 1, "weights": 2, "sources": 3},

@@ -209,9 +209,26 @@ gbf_status gbf_widest_path(gbf_graph *g, int32_t src, int32_t *width, int mem,
                            const gbf_options *opt, void *cuda_stream);
 
 /*
+ * gbf_betweenness — single-source betweenness centrality (§4 "Single-Source
+ * Betweenness Centrality"; Alg. 2): a forward pass of frontier rounds that
+ * counts shortest paths with fp64 fetch-and-add and keeps every frontier,
+ * then a backward pass over those frontiers in reverse that accumulates
+ * dependencies.  Works on the graph's arcs; weights are ignored.
+ *   dep     double[n]: dep[v] = sum over targets t of the fraction of
+ *           shortest src-t paths through v (v != src); dep[src] = the number
+ *           of other vertices reached; 0 where unreachable.  fp64, summation
+ *           order varies between runs (relative differences ~1e-15).
+ *   mem     GBF_HOST: blocks; GBF_DEVICE: stream-ordered, see gbf_wait
+ * Errors: as gbf_bfs; GBF_ERR_OVERFLOW if the search has more than 65,536
+ * levels.
+ */
+gbf_status gbf_betweenness(gbf_graph *g, int32_t src, double *dep, int mem,
+                           const gbf_options *opt, void *cuda_stream);
+
+/*
  * gbf_wait — synchronise `cuda_stream` and return the device-side status of
  * the last gbf_bfs / gbf_wbfs / gbf_msbfs / gbf_bellman_ford /
- * gbf_widest_path issued on g with GBF_DEVICE
+ * gbf_widest_path / gbf_betweenness issued on g with GBF_DEVICE
  * buffers; fills *stats if non-NULL.
  */
 gbf_status gbf_wait(gbf_graph *g, void *cuda_stream, gbf_stats *stats);

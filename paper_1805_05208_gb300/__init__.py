@@ -102,6 +102,7 @@ def _load() -> ctypes.CDLL:
         "gbf_wbfs": (S, [P, I32, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
         "gbf_bellman_ford": (S, [P, I32, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
         "gbf_widest_path": (S, [P, I32, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
+        "gbf_betweenness": (S, [P, I32, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
         "gbf_wait": (S, [P, P, ctypes.POINTER(gbf_stats)]),
         "gbf_msbfs": (S, [P, P, I32, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
         "gbf_server_options_default": (S, [ctypes.POINTER(gbf_server_options)]),
@@ -238,6 +239,14 @@ def gbf_widest_path(h: int, src: int, width, opt: Optional[gbf_options] = None,
     pd, mem = _ptr(width)
     _check(_lib.gbf_widest_path(h, int(src), pd, mem, _opt(opt), _stream(stream)),
            "gbf_widest_path")
+
+
+def gbf_betweenness(h: int, src: int, dep, opt: Optional[gbf_options] = None,
+                    stream=None) -> None:
+    """Single-source betweenness dependencies from src into dep (float64)."""
+    pd, mem = _ptr(dep)
+    _check(_lib.gbf_betweenness(h, int(src), pd, mem, _opt(opt), _stream(stream)),
+           "gbf_betweenness")
 
 
 def gbf_msbfs(h: int, srcs, dist, opt: Optional[gbf_options] = None, stream=None) -> None:
@@ -403,6 +412,11 @@ class Graph:
     def widest_path(self, src: int, opt=None):
         d = np.empty(self.n, dtype=np.int32)
         gbf_widest_path(self.h, src, d, opt)
+        return d
+
+    def betweenness(self, src: int, opt=None):
+        d = np.empty(self.n, dtype=np.float64)
+        gbf_betweenness(self.h, src, d, opt)
         return d
 
     def stats(self, stream=None) -> dict:

@@ -106,6 +106,15 @@ struct Workspace {
   cudaGraphExec_t ms_exec = nullptr;
   long long ms_key[6] = {0, 0, 0, 0, 0, 0};
   int ms_grid = 0;
+  // betweenness (lazy): path counts / coefficients, levels, chunk starts of
+  // every level, per-level descriptors, fp64 output staging for host buffers
+  double *bc_paths = nullptr;
+  int32_t *bc_lvl = nullptr;
+  uint32_t *bc_cs = nullptr;
+  uint32_t bc_cs_total = 0;
+  void *bc_info = nullptr;
+  int bc_max_levels = 0;
+  double *bc_out_tmp = nullptr;
   // pinned host copy of the control block
   Ctl *ctl_host = nullptr;
   int last_kind = 0;   // 1 bfs, 2 wbfs, 3 msbfs
@@ -143,6 +152,7 @@ gbf_status check_smem(size_t bytes, const char *kernel);
 gbf_status ws_ensure_base(Graph &g, Workspace &ws);
 gbf_status ws_ensure_wbfs(Graph &g, Workspace &ws, int nB);
 gbf_status ws_ensure_msbfs(Graph &g, Workspace &ws, bool host_out);
+gbf_status ws_ensure_bc(Graph &g, Workspace &ws);
 void ws_free(Workspace &ws);
 gbf_status ws_collect(Workspace &ws, cudaStream_t st, gbf_stats *stats);
 

@@ -278,13 +278,32 @@ gbf_status ws_ensure_msbfs(Graph &g, Workspace &ws, bool host_out) {
   return GBF_OK;
 }
 
+gbf_status ws_ensure_bc(Graph &g, Workspace &ws) {
+  GBF_TRY(ws_ensure_base(g, ws));
+  if (ws.bc_paths) return GBF_OK;
+  const size_t n = (size_t)g.n;
+  size_t acc = 0;
+  ws.bc_max_levels = 1 << 16;
+  ws.bc_cs_total = (uint32_t)(((uint64_t)g.m + dev::kFine - 1) / dev::kFine + 2 * (uint64_t)ws.bc_max_levels + 2);
+  GBF_TRY(dmalloc(&ws.bc_paths, n, acc));
+  GBF_TRY(dmalloc(&ws.bc_lvl, n, acc));
+  GBF_TRY(dmalloc(&ws.bc_cs, (size_t)ws.bc_cs_total, acc));
+  uint4 *info = nullptr;
+  GBF_TRY(dmalloc(&info, (size_t)ws.bc_max_levels, acc));
+  ws.bc_info = info;
+  GBF_TRY(dmalloc(&ws.bc_out_tmp, n, acc));
+  ws.bytes += acc;
+  return GBF_OK;
+}
+
 void ws_free(Workspace &ws) {
   void *ptrs[] = {ws.visited, ws.fbm[0], ws.fbm[1], ws.fbm[2], ws.q[0], ws.q[1], ws.qoff[0], ws.qoff[1],
                   ws.qadj[0], ws.qadj[1], ws.ms_qadj[2],
                   ws.cs[0], ws.cs[1], ws.ctl, ws.dist_tmp, ws.parent_tmp, ws.trace, ws.slots,
                   ws.slot_cnt, ws.ovf[0], ws.ovf[1], ws.ms_seen, ws.ms_visit, ws.ms_next,
                   ws.ms_q[2], ws.ms_qoff[2], ws.ms_cs[2], ws.ms_touched, ws.ms_call,
-                  ws.ms_dist_tmp};
+                  ws.ms_dist_tmp, ws.bc_paths, ws.bc_lvl, ws.bc_cs, ws.bc_info,
+                  ws.bc_out_tmp};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (ws.ctl_host) cudaFreeHost(ws.ctl_host);
