@@ -3,9 +3,9 @@
 A plain serial CPU statement of what the traversal path computes, written
 from the paper's problem statements (§4, "Breadth-First Search",
 "Integral-Weight SSSP", "General-Weight SSSP (Bellman-Ford)", "Widest
-Path", "Single-Source Betweenness Centrality"): hop distances,
-shortest-path distances, widest-path widths and betweenness dependencies,
-each the unique answer to its definition.  ``oracle.c`` holds the arithmetic (FIFO
+Path", "Single-Source Betweenness Centrality", "k-core"): hop distances,
+shortest-path distances, widest-path widths, betweenness dependencies and
+corenesses, each the unique answer to its definition.  ``oracle.c`` holds the arithmetic (FIFO
 BFS, binary-heap Dijkstra, Floyd–Warshall, output validators); this module
 only marshals numpy arrays into it.
 
@@ -65,6 +65,8 @@ def _load():
             lib.or_bellman_ford.restype = ctypes.c_int64
             lib.or_betweenness.argtypes = [ctypes.c_int32, P, P, ctypes.c_int32, P, P, P]
             lib.or_betweenness.restype = ctypes.c_int64
+            lib.or_coreness.argtypes = [ctypes.c_int32, P, P, P]
+            lib.or_coreness.restype = ctypes.c_int64
             lib.or_floyd_warshall.argtypes = [ctypes.c_int32, P, P, P, P]
             lib.or_floyd_warshall.restype = ctypes.c_int
             lib.or_check_bfs.argtypes = [ctypes.c_int32, P, P, ctypes.c_int32, P, P,
@@ -162,6 +164,19 @@ def betweenness(g, src: int, full: bool = False):
     if rc < 0:
         raise ValueError("or_betweenness: bad argument")
     return (D, paths, level) if full else D
+
+
+def coreness(g):
+    """Coreness of every vertex (int32): the largest k such that the vertex
+    lies in a subgraph of minimum degree k."""
+    lib = _load()
+    off, po = _c(g.off, np.uint32)
+    tgt = np.ascontiguousarray(g.tgt, dtype=np.int32) if g.m else np.zeros(1, np.int32)
+    core = np.empty(g.n, dtype=np.int32)
+    rc = lib.or_coreness(g.n, po, tgt.ctypes.data, core.ctypes.data)
+    if rc < 0:
+        raise ValueError("or_coreness: bad argument")
+    return core
 
 
 def floyd_warshall(g, weighted: bool):

@@ -22,7 +22,12 @@
  *     recording each round's frontier, then a backward pass over the
  *     recorded frontiers in reverse accumulating dependencies, in fp64; it
  *     is pinned against the definition (sums of path-count ratios over all
- *     targets) computed by brute force.  Floyd–Warshall is included as a brute-force check for tiny
+ *     targets) computed by brute force.
+ *   - k-core (coreness, §4 "k-core"; Alg. 16): the coreness of v is the
+ *     largest k such that v lies in a subgraph whose vertices all have
+ *     degree >= k.  The oracle is the textbook bucket peeling (repeatedly
+ *     remove a vertex of minimum current degree; its coreness is the largest
+ *     minimum seen so far), pinned against the definition by brute force.  Floyd–Warshall is included as a brute-force check for tiny
  * graphs.  Infinity is INT32_MAX; unreachable parents are -1; the parent of
  * the source is the source itself.
  *
@@ -301,6 +306,64 @@ int64_t or_betweenness(int32_t n, const uint32_t *off, const int32_t *tgt, int32
   free(order);
   free(lo);
   return nl;
+}
+
+/* ------------------------------------------------------- coreness */
+/* Bucket peeling: vertices sit in buckets by current degree; repeatedly take
+ * a vertex from the lowest non-empty bucket (never below the running k),
+ * give it coreness k = max(k, its degree), and lower each remaining
+ * neighbour's degree by one, moving it one bucket down.  Buckets are doubly
+ * linked lists.  Returns the largest coreness, or -1 on a bad argument. */
+int64_t or_coreness(int32_t n, const uint32_t *off, const int32_t *tgt, int32_t *core) {
+  if (n <= 0) return -1;
+  int32_t maxd = 0;
+  for (int32_t v = 0; v < n; v++) {
+    const int32_t d = (int32_t)(off[v + 1] - off[v]);
+    if (d > maxd) maxd = d;
+  }
+  int32_t *deg = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+  int32_t *head = (int32_t *)malloc(sizeof(int32_t) * ((size_t)maxd + 1));
+  int32_t *nxt = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+  int32_t *prv = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+  char *done = (char *)calloc((size_t)n, 1);
+  if (!deg || !head || !nxt || !prv || !done) {
+    free(deg); free(head); free(nxt); free(prv); free(done);
+    return -1;
+  }
+  for (int32_t d = 0; d <= maxd; d++) head[d] = -1;
+  for (int32_t v = 0; v < n; v++) {
+    deg[v] = (int32_t)(off[v + 1] - off[v]);
+    prv[v] = -1;
+    nxt[v] = head[deg[v]];
+    if (head[deg[v]] >= 0) prv[head[deg[v]]] = v;
+    head[deg[v]] = v;
+  }
+  int32_t k = 0, lo = 0;
+  for (int32_t removed = 0; removed < n; removed++) {
+    while (head[lo] < 0) lo++;
+    const int32_t v = head[lo];
+    head[lo] = nxt[v];
+    if (nxt[v] >= 0) prv[nxt[v]] = -1;
+    done[v] = 1;
+    if (deg[v] > k) k = deg[v];
+    core[v] = k;
+    for (uint32_t e = off[v]; e < off[v + 1]; e++) {
+      const int32_t u = tgt[e];
+      if (done[u] || deg[u] <= lo) continue;  /* never below the current minimum */
+      const int32_t d = deg[u];
+      /* unlink u from bucket d, relink in d - 1 */
+      if (prv[u] >= 0) nxt[prv[u]] = nxt[u];
+      else head[d] = nxt[u];
+      if (nxt[u] >= 0) prv[nxt[u]] = prv[u];
+      deg[u] = d - 1;
+      prv[u] = -1;
+      nxt[u] = head[d - 1];
+      if (head[d - 1] >= 0) prv[head[d - 1]] = u;
+      head[d - 1] = u;
+    }
+  }
+  free(deg); free(head); free(nxt); free(prv); free(done);
+  return k;
 }
 
 /* --------------------------------------------------------- Floyd–Warshall */
