@@ -56,6 +56,9 @@ WORKLOADS = {
     "bc-rmat22": dict(kind="bc", graph="rmat", scale=22, ef=16, w=None, nsrc=8,
                       desc="single-source betweenness (Alg. 2, forward path counts + backward "
                            "dependencies, fp64), RMAT scale 22 ef16, 8 seeded sources"),
+    "kcore-rmat22": dict(kind="kcore", graph="rmat", scale=22, ef=16, w=None, nsrc=1,
+                         desc="coreness of every vertex (Alg. 16 peeling), RMAT scale 22 ef16; "
+                              "one step = one full decomposition; GTEPS = undirected edges / time"),
     "wbfs-rmat26": dict(kind="wbfs", graph="rmat", scale=26, ef=16, w=(1, 22), nsrc=2,
                         desc="wBFS, RMAT scale 26 ef16, w in [1,22), 2 seeded sources"),
     "msbfs-rmat24": dict(kind="msbfs", graph="rmat", scale=24, ef=16, w=None, nsrc=64,
@@ -116,7 +119,7 @@ def make_sources(g, wl, rank=0):
 
 ORACLE_NAME = {"bfs": "FIFO BFS", "wbfs": "binary-heap Dijkstra",
                "bf": "frontier Bellman-Ford", "widest": "(max,min) Bellman-Ford rounds",
-               "bc": "betweenness forward + backward passes"}
+               "bc": "betweenness forward + backward passes", "kcore": "bucket peeling"}
 
 
 def reach_of(kind, g, src, out):
@@ -195,6 +198,10 @@ KERNEL_SOURCES = {
     "bfs_kernel": ("bfs.cu", "dev_common.cuh", "gbf_impl.h"),
     "wbfs_kernel": ("wbfs.cu", "dev_common.cuh", "gbf_impl.h"),
     "msbfs_kernel": ("msbfs.cu", "dev_common.cuh", "gbf_impl.h"),
+    "bf_kernel": ("bellman_ford.cu", "dev_common.cuh", "gbf_impl.h"),
+    "widest_kernel": ("bellman_ford.cu", "dev_common.cuh", "gbf_impl.h"),
+    "bc_kernel": ("betweenness.cu", "dev_common.cuh", "gbf_impl.h"),
+    "kcore_kernel": ("kcore.cu", "dev_common.cuh", "gbf_impl.h"),
 }
 
 
@@ -235,6 +242,14 @@ def bytes_model(kind, n, st):
         # and the bucket write (8); per heavy vertex: queue + degree prefix
         # written and read (16)
         return 4 * n + 16 * I + 12 * E + 8 * R + 16 * st["heavy_vertices"]
+    if kind == "kcore":
+        # init remaining degrees and the finished bitmap (4n + n/8); per
+        # bucket k two passes over them (remaining degree and finished word
+        # of every vertex); per arc of a peeled vertex: target, its remaining
+        # degree, the fetch-and-add (12); per vertex: queue entry written and
+        # read, coreness written (16)
+        nk = st.get("buckets", 1)
+        return 4 * n + n // 8 + nk * 2 * (4 * n + n // 8) + 12 * E + 16 * n
     if kind == "bc":
         # init path counts, dependencies (fp64) and levels (20n); per scanned
         # arc in either pass: target, its level, one 8-byte value (16); per
@@ -296,6 +311,9 @@ def cpu_reference_sample(g, wl, srcs, budget_s=15.0, max_queries=None):
         elif wl["kind"] == "bc":
             _, _, lv = oracle.betweenness(g, int(s), full=True)
             d = np.where(lv >= 0, lv, INF)
+        elif wl["kind"] == "kcore":
+            oracle.coreness(g)
+            d = np.zeros(g.n, dtype=np.int64)  # every edge is processed
         else:
             d, _ = oracle.bfs(g, int(s))
         t += time.perf_counter() - t0
@@ -646,6 +664,8 @@ def main():
             gb.gbf_widest_path(graph.h, int(srcs[i]), outs[i], opt, stream)
         elif kind == "bc":
             gb.gbf_betweenness(graph.h, int(srcs[i]), outs[i], opt, stream)
+        elif kind == "kcore":
+            gb.gbf_kcore(graph.h, outs[i], opt, stream)
         else:
             gb.gbf_bfs(graph.h, int(srcs[i]), outs[i], pars[i], opt, stream)
 
@@ -656,7 +676,10 @@ def main():
             launch(i)
             if w == 0:
                 stats.append(gb.gbf_wait(graph.h, stream))
-                if kind == "bc":
+                if kind == "kcore":
+                    te.append(g.m // 2)
+                    stats[-1]["buckets"] = int(np.unique(outs[i].cpu().numpy()).size)
+                elif kind == "bc":
                     # the component, from one untimed BFS of this library
                     hops = torch.empty(n, dtype=torch.int32, device=dev)
                     gb.gbf_bfs(graph.h, int(srcs[i]), hops, None, None, stream)
@@ -725,6 +748,8 @@ def main():
                 gb.gbf_widest_path(graph.h, int(srcs[i]), host_out[i], opt, None)
             elif kind == "bc":
                 gb.gbf_betweenness(graph.h, int(srcs[i]), host_out[i], opt, None)
+            elif kind == "kcore":
+                gb.gbf_kcore(graph.h, host_out[i], opt, None)
             else:
                 gb.gbf_bfs(graph.h, int(srcs[i]), host_out[i], host_par[i], opt, None)
     e2e_s = time.perf_counter() - t0

@@ -226,9 +226,23 @@ gbf_status gbf_betweenness(gbf_graph *g, int32_t src, double *dep, int mem,
                            const gbf_options *opt, void *cuda_stream);
 
 /*
+ * gbf_kcore — the coreness of every vertex (§4 "k-core"; Alg. 16): for k in
+ * increasing order, the unfinished vertices whose remaining degree is at
+ * most k are finished with coreness k and peeled in rounds of the blocked
+ * sparse edgeMap, each lowering its unfinished neighbours' remaining degree
+ * by its number of arcs to them (combined per warp window); a neighbour that
+ * reaches k is finished in the same bucket.
+ *   core    int32[n]: coreness (0 for isolated vertices)
+ *   mem     GBF_HOST: blocks; GBF_DEVICE: stream-ordered, see gbf_wait
+ * Errors: GBF_ERR_INVALID for NULL arguments; GBF_ERR_TIMEOUT as gbf_bfs.
+ */
+gbf_status gbf_kcore(gbf_graph *g, int32_t *core, int mem, const gbf_options *opt,
+                     void *cuda_stream);
+
+/*
  * gbf_wait — synchronise `cuda_stream` and return the device-side status of
  * the last gbf_bfs / gbf_wbfs / gbf_msbfs / gbf_bellman_ford /
- * gbf_widest_path / gbf_betweenness issued on g with GBF_DEVICE
+ * gbf_widest_path / gbf_betweenness / gbf_kcore issued on g with GBF_DEVICE
  * buffers; fills *stats if non-NULL.
  */
 gbf_status gbf_wait(gbf_graph *g, void *cuda_stream, gbf_stats *stats);

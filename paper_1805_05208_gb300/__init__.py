@@ -103,6 +103,7 @@ def _load() -> ctypes.CDLL:
         "gbf_bellman_ford": (S, [P, I32, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
         "gbf_widest_path": (S, [P, I32, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
         "gbf_betweenness": (S, [P, I32, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
+        "gbf_kcore": (S, [P, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
         "gbf_wait": (S, [P, P, ctypes.POINTER(gbf_stats)]),
         "gbf_msbfs": (S, [P, P, I32, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
         "gbf_server_options_default": (S, [ctypes.POINTER(gbf_server_options)]),
@@ -247,6 +248,12 @@ def gbf_betweenness(h: int, src: int, dep, opt: Optional[gbf_options] = None,
     pd, mem = _ptr(dep)
     _check(_lib.gbf_betweenness(h, int(src), pd, mem, _opt(opt), _stream(stream)),
            "gbf_betweenness")
+
+
+def gbf_kcore(h: int, core, opt: Optional[gbf_options] = None, stream=None) -> None:
+    """Coreness of every vertex into core (int32)."""
+    pd, mem = _ptr(core)
+    _check(_lib.gbf_kcore(h, pd, mem, _opt(opt), _stream(stream)), "gbf_kcore")
 
 
 def gbf_msbfs(h: int, srcs, dist, opt: Optional[gbf_options] = None, stream=None) -> None:
@@ -417,6 +424,11 @@ class Graph:
     def betweenness(self, src: int, opt=None):
         d = np.empty(self.n, dtype=np.float64)
         gbf_betweenness(self.h, src, d, opt)
+        return d
+
+    def kcore(self, opt=None):
+        d = np.empty(self.n, dtype=np.int32)
+        gbf_kcore(self.h, d, opt)
         return d
 
     def stats(self, stream=None) -> dict:
