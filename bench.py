@@ -235,12 +235,12 @@ def bytes_model(kind, n, st):
     word, random or not), from the device statistics of the query."""
     E, V, R, I = st["edges_scanned"], st["vertices_expanded"], st["relaxations"], st["bucket_inserts"]
     if kind == "wbfs":
-        # init D (4n); per bucket entry read at extraction: ring slot, D[v],
-        # offsets pair (16; entries = filings I, stale ones included); per
-        # scanned arc: tgt, w, D[v] (12); per successful writeMin: atomicMin
-        # and the bucket write (8); per heavy vertex: queue + degree prefix
-        # written and read (16)
-        return 4 * n + 16 * I + 12 * E + 8 * R + 16 * st["heavy_vertices"]
+        # init D (4n); per filing: the bucket write, then at extraction the
+        # ring slot, D[v], offsets pair (20; filings I, stale ones included,
+        # degree-1 vertices not filed); per scanned arc: tgt, w, D[v] (12);
+        # per successful writeMin: atomicMin and the degree-1 bitmap word (8);
+        # per heavy vertex: queue + degree prefix written and read (16)
+        return 4 * n + 20 * I + 12 * E + 8 * R + 16 * st["heavy_vertices"]
     if kind == "kcore":
         # init remaining degrees and the finished bitmap (4n + n/8); per
         # bucket k two passes over them (remaining degree and finished word
@@ -278,7 +278,7 @@ def bytes_model(kind, n, st):
 def trace_summary(tr):
     """Per-kind round counts and device time of one query's round trace."""
     out, prev = {}, 0
-    names = {1: "sparse", 2: "dense", 3: "sparse+heavy", 4: "conversion"}
+    names = {1: "sparse", 2: "dense", 3: "sparse+heavy", 4: "conversion", 5: "bucket"}
     for (_, kind, fr, fe, t, _tm) in tr:
         k = names.get(kind, str(kind))
         d = out.setdefault(k, {"rounds": 0, "us": 0.0, "frontier": 0})

@@ -362,7 +362,8 @@ gbf_status gbf_server_destroy(gbf_server *s);
 /* One record per round of the last query (see gbf_trace). */
 typedef struct {
   int32_t round;          /* 1-based round (BFS level or wBFS bucket round) */
-  int32_t kind;           /* 1 sparse, 2 dense, 3 sparse + heavy pass, 4 conversion */
+  int32_t kind;           /* 1 sparse, 2 dense, 3 sparse + heavy pass, 4 conversion,
+                             5 k-core bucket pass (frontier = the bucket) */
   uint32_t frontier;      /* frontier vertices (wBFS: bucket entries, stale ones included) */
   uint32_t frontier_edges;/* out-degree sum of the frontier when known (0 otherwise) */
   int64_t t_ns;           /* device time at the end of the round, since the kernel started */
@@ -370,8 +371,8 @@ typedef struct {
 } gbf_round_trace;
 
 /*
- * gbf_trace — per-round device timeline of the last gbf_bfs / gbf_wbfs on g
- * (the round structure of Alg. 1 / Alg. 3 as it ran: direction chosen,
+ * gbf_trace — per-round device timeline of the last query on g (the round
+ * structure of Alg. 1 / Alg. 3 / Alg. 16 as it ran: direction chosen,
  * frontier size, time).  Call after the query completed (host buffers, or
  * after gbf_wait).  Copies min(rounds, cap) records to out and their number
  * to *count.

@@ -131,6 +131,7 @@ struct Graph {
   uint32_t *off = nullptr;
   int32_t *tgt = nullptr;
   uint32_t *w = nullptr;
+  uint32_t *leaf = nullptr;  // bit v set iff deg(v) == 1 (wBFS does not file these)
   size_t bytes = 0;
   Workspace ws;
   std::mutex mu;   // serialises host calls on the default workspace

@@ -160,6 +160,17 @@ __global__ void k_digest(int32_t n, uint32_t m, const uint32_t *off, const int32
   }
 }
 
+// Bit v of leaf[] is set iff vertex v has degree exactly 1.
+__global__ void k_leaf(int32_t n, const uint32_t *off, uint32_t *leaf) {
+  const uint32_t nw = ((uint32_t)n + 31) >> 5;
+  const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  for (uint32_t i = gt; i < nw * 32u; i += gs) {
+    const bool one = i < (uint32_t)n && off[i + 1] - off[i] == 1u;
+    const unsigned b = __ballot_sync(0xffffffffu, one);
+    if ((threadIdx.x & 31) == 0) leaf[i >> 5] = b;
+  }
+}
+
 template <class T>
 gbf_status dmalloc(T **p, size_t count, size_t &acc) {
   *p = nullptr;
@@ -411,6 +422,7 @@ gbf_status gbf_graph_create(int32_t n, const uint32_t *off, const int32_t *tgt, 
   if ((s = dmalloc(&g.off, (size_t)n + 1, acc)) != GBF_OK) return fail(s);
   if ((s = dmalloc(&g.tgt, (size_t)m, acc)) != GBF_OK) return fail(s);
   if (w && (s = dmalloc(&g.w, (size_t)m, acc)) != GBF_OK) return fail(s);
+  if ((s = dmalloc(&g.leaf, ((size_t)n + 31) / 32, acc)) != GBF_OK) return fail(s);
   g.bytes = acc;
   const cudaMemcpyKind kind = mem == GBF_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   cudaError_t e;
@@ -444,7 +456,10 @@ gbf_status gbf_graph_create(int32_t n, const uint32_t *off, const int32_t *tgt, 
   if (haux.flags == 0 && (validate_flags & GBF_VALIDATE_SYMMETRIC)) {
     k_validate_symmetric<<<grid, 256, 0, st>>>(n, g.off, g.tgt, g.w, &aux->flags);
   }
-  if (haux.flags == 0) k_digest<<<grid, 256, 0, st>>>(n, m, g.off, g.tgt, g.w, &aux->sum, &aux->wmax);
+  if (haux.flags == 0) {
+    k_digest<<<grid, 256, 0, st>>>(n, m, g.off, g.tgt, g.w, &aux->sum, &aux->wmax);
+    k_leaf<<<grid, 256, 0, st>>>(n, g.off, g.leaf);
+  }
   e = cudaStreamSynchronize(st);
   if (e == cudaSuccess) e = cudaMemcpy(&haux, aux, sizeof(Aux), cudaMemcpyDeviceToHost);
   cudaFree(aux);
@@ -478,6 +493,7 @@ gbf_status gbf_graph_destroy(gbf_graph *h) {
   if (g.off) cudaFree(g.off);
   if (g.tgt) cudaFree(g.tgt);
   if (g.w) cudaFree(g.w);
+  if (g.leaf) cudaFree(g.leaf);
   delete h;
   return GBF_OK;
 }

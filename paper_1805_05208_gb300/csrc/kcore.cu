@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(1024) kcore_kernel(KcParams P) {
   // CTA-contiguous word ranges for the vertex passes
   const uint32_t per = (nwords + gridDim.x - 1) / gridDim.x;
   const uint32_t wlo = min(nwords, blockIdx.x * per), whi = min(nwords, wlo + per);
-  int bem = 0, sub = 0;
+  int bem = 0, sub = 0, tr = 0;  // tr: trace records (bucket passes and peeling rounds)
   for (int it = 0; ok; it++) {
     // ---------------- NextBucket: smallest D over unfinished vertices
     if (blockIdx.x == 0 && threadIdx.x == 0) st_vol(ctl->gmin[(it + 1) & 1], kInf);
@@ -183,6 +183,13 @@ __global__ void __launch_bounds__(1024) kcore_kernel(KcParams P) {
     // ---------------- peeling rounds within bucket k
     int qb = 0;
     unsigned long long fr = ld_vol(ctl->fr[sub % 3]);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      atomicAdd(&ctl->rounds, 1);
+      if (P.trace && tr < P.trace_cap)
+        P.trace[tr] = TraceRec{tr + 1, 5, (uint32_t)(fr >> 32), (uint32_t)fr,
+                               (long long)(globaltimer() - t_start), 0};
+    }
+    tr++;
     while (ok) {
       const uint32_t cnt = (uint32_t)(fr >> 32), Dsum = (uint32_t)fr;
       if (cnt == 0) break;
@@ -209,8 +216,9 @@ __global__ void __launch_bounds__(1024) kcore_kernel(KcParams P) {
         break;
       }
       fr = ld_vol(*outc);
-      if (P.trace && blockIdx.x == 0 && threadIdx.x == 0 && sub <= P.trace_cap)
-        P.trace[sub - 1] = TraceRec{sub, 1, cnt, Dsum, (long long)(globaltimer() - t_start), 0};
+      if (P.trace && blockIdx.x == 0 && threadIdx.x == 0 && tr < P.trace_cap)
+        P.trace[tr] = TraceRec{tr + 1, 1, cnt, Dsum, (long long)(globaltimer() - t_start), 0};
+      tr++;
     }
     sub++;  // the bucket pass of the next k uses a fresh counter slot
     if (blockIdx.x == 0 && threadIdx.x == 0) st_vol(ctl->fr[(sub + 1) % 3], 0ull);

@@ -42,6 +42,7 @@ using namespace dev;
 
 struct WbfsParams {
   DevGraph g;
+  const uint32_t *leaf;  // bit v set iff deg(v) == 1
   int32_t src;
   int32_t *dist;
   int32_t *slots;
@@ -70,6 +71,7 @@ struct WbfsParams {
 namespace {
 
 constexpr int kMaskWords = 8;  // pending / filed slot masks: nB <= 256
+constexpr int32_t kNoSlot = -1;  // a staged entry dropped at the flush (overflow slots are <= -2)
 
 struct Counters {
   unsigned long long scanned, relax, inserts, expanded, heavy;
@@ -193,7 +195,16 @@ struct FileSink {
       S.misc[7] = (uint32_t)kInf;
     }
     __syncthreads();
+    // A vertex of degree 1 lowered here was lowered through its only
+    // neighbour, whose distance is final: its own distance is final too and
+    // expanding it could not lower anything, so it is not filed (its entry
+    // would only be extracted and skipped).  The source is never filed here.
     for (uint32_t i = threadIdx.x; i < k; i += blockDim.x) {
+      const int32_t v = S.fv[i];
+      if ((__ldg(P->leaf + (v >> 5)) >> (v & 31)) & 1u) {
+        S.fs[i] = kNoSlot;
+        continue;
+      }
       const int32_t sl = S.fs[i];
       if (sl >= 0) {
         S.pref[i] = atomicAdd(&S.hist[sl], 1u);
@@ -222,16 +233,18 @@ struct FileSink {
     for (uint32_t i = threadIdx.x; i < k; i += blockDim.x) {
       const int32_t sl = S.fs[i];
       const int32_t v = S.fv[i];
+      if (sl == kNoSlot) continue;
       if (sl >= 0) {
         const uint32_t pos = (S.gbase[sl] + S.pref[i]) % n;
         P->slots[(size_t)sl * n + pos] = v;
+        c->inserts++;
       } else {
         const uint32_t pos = S.misc[6] + S.pref[i];
         if (pos < P->ovf_cap) P->ovf[cur][pos] = make_int2(v, -sl - 2);
         else raise_error(P->ctl, GBF_ERR_OVERFLOW, 6);
+        c->inserts++;
       }
     }
-    if (threadIdx.x == 0) c->inserts += k;
     __syncthreads();
     if (threadIdx.x == 0) S.misc[4] = 0;
     __syncthreads();
@@ -567,8 +580,10 @@ __global__ void __launch_bounds__(1024) wbfs_kernel(WbfsParams P) {
 
 gbf_status launch_wbfs(Graph &g, Workspace &ws, int32_t src, int32_t *dist, const Opts &o,
                        cudaStream_t st) {
+  if (!g.leaf) return set_error("graph has no degree-1 bitmap"), GBF_ERR_INVALID;
   WbfsParams P;
   P.g = g.dev();
+  P.leaf = g.leaf;
   P.src = src;
   P.dist = dist;
   P.slots = ws.slots;
