@@ -25,7 +25,7 @@ def test_bytes_model_terms():
     st = dict(edges_scanned=10, vertices_expanded=3, relaxations=4, bucket_inserts=5,
               vertices_reached=6, pull_rounds=1, heavy_vertices=2)
     n = 64
-    assert bench.bytes_model("wbfs", n, st) == 4 * n + 16 * 5 + 12 * 10 + 8 * 4 + 16 * 2
+    assert bench.bytes_model("wbfs", n, st) == 4 * n + 20 * 5 + 12 * 10 + 8 * 4 + 16 * 2
     assert bench.bytes_model("bfs", n, st) == 8 * n + n // 8 + 12 * 3 + 8 * 10 + 24 * 6 + 3 * (n // 8)
 
 
