@@ -34,7 +34,7 @@ struct Ctl {
   unsigned long long conv;     // conversion cursor (same packing)
   // wBFS
   unsigned int mcnt[2];        // moved-list counts, by round parity
-  int gmin[2];                 // min distance lowered in the round, by parity
+  int gmin[3];                 // k-core: smallest remaining degree of the next bucket, by bucket % 3
   unsigned int ovf_cnt[2];     // overflow bucket counts
   int ovf_min[2];              // overflow bucket minimum value
   unsigned int imask[3][32];   // buckets filed into during round t, by t % 3 (one bit per slot)

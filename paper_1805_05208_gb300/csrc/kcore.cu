@@ -1,9 +1,13 @@
 // Coreness of every vertex (§4 "k-core"; Alg. 16, the bucketing peeling of
 // Julienne) as one persistent cooperative kernel.  D starts at the degrees.
 // For each k in increasing order:
-//   - NextBucket: k = the smallest D over unfinished vertices (one pass over
-//     the vertices, a CTA min and one atomicMin), so empty buckets cost
-//     nothing;
+//   - NextBucket: k = the smallest D over unfinished vertices.  It is
+//     gathered while the previous bucket runs, with no pass of its own:
+//     its vertex pass sees every untouched unfinished D, and a decrement
+//     that leaves a vertex above the previous k offers its new D.  An
+//     offered value may belong to a vertex finished later in the same
+//     bucket, so k can fall below the true minimum; the bucket is then
+//     empty and only costs its pass.  Empty buckets are otherwise skipped;
 //   - the bucket: every unfinished vertex with D <= k is finished with
 //     coreness k and put on a frontier queue (CTA-staged compaction);
 //   - peeling rounds: the blocked sparse edgeMap over the frontier lowers
@@ -56,16 +60,31 @@ struct PeelFn {
   uint32_t *fin;
   int32_t k;
   unsigned long long peeled;
+  int32_t nmin;  // smallest D left above k by this thread's decrements
+  // Applies one decrement of c to v; true if v crossed into bucket k.
+  __device__ __forceinline__ bool decrement(int32_t v, int32_t c) {
+    const int32_t old = atomicSub(D + v, c);
+    if (old - c > k) nmin = min(nmin, old - c);
+    if (old > k && old - c <= k) {  // crossed into bucket k: finished now
+      core[v] = k;
+      atomicOr(fin + (v >> 5), 1u << (v & 31));
+      peeled++;
+      return true;
+    }
+    return false;
+  }
   template <class Sink>
   __device__ __forceinline__ void batch(const bool *ok, const int32_t *, const uint32_t *idx,
                                         Sink &sink, PushSmem &S) {
     const int lane = threadIdx.x & 31;
-    int32_t v[kU];
+    int32_t v[kU], dv[kU];
     bool live[kU];
 #pragma unroll
     for (int r = 0; r < kU; r++) v[r] = ok[r] ? __ldg(tgt + idx[r]) : 0;
 #pragma unroll
-    for (int r = 0; r < kU; r++) live[r] = ok[r] && __ldcg(D + v[r]) > k;
+    for (int r = 0; r < kU; r++) dv[r] = ok[r] ? __ldcg(D + v[r]) : 0;
+#pragma unroll
+    for (int r = 0; r < kU; r++) live[r] = ok[r] && dv[r] > k;
     bool win[kU];
 #pragma unroll
     for (int r = 0; r < kU; r++) {
@@ -73,16 +92,7 @@ struct PeelFn {
       // one fetch-and-add per distinct neighbour of the window
       const uint32_t key = live[r] ? (uint32_t)v[r] : (0x80000000u | (uint32_t)lane);
       const unsigned grp = __match_any_sync(kFull, key);
-      if (live[r] && lane == __ffs(grp) - 1) {
-        const int32_t c = __popc(grp);
-        const int32_t old = atomicSub(D + v[r], c);
-        if (old > k && old - c <= k) {  // crossed into bucket k: finished now
-          win[r] = true;
-          core[v[r]] = k;
-          atomicOr(fin + (v[r] >> 5), 1u << (v[r] & 31));
-          peeled++;
-        }
-      }
+      if (live[r] && lane == __ffs(grp) - 1) win[r] = decrement(v[r], __popc(grp));
     }
     uint32_t a[kU], z[kU];
 #pragma unroll
@@ -97,6 +107,7 @@ struct PeelFn {
     sink.template append_n<kU>(S, win, v, z, a);
   }
 };
+
 
 }  // namespace
 
@@ -116,10 +127,12 @@ __global__ void __launch_bounds__(1024) kcore_kernel(KcParams P) {
   unsigned long long scanned = 0, peeled = 0;
   const unsigned long long t_start = globaltimer();
 
+  // D = degrees.  The first bucket is k = 0 (isolated vertices; empty if
+  // there are none), whose pass gathers the smallest degree above 0.
   for (uint32_t i = gt; i < n; i += gs) P.D[i] = (int32_t)(__ldg(g.off + i + 1) - __ldg(g.off + i));
   for (uint32_t i = gt; i < nwords; i += gs) P.fin[i] = 0u;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
-    st_vol(ctl->gmin[0], kInf);
+    st_vol(ctl->gmin[0], 0);
     st_vol(ctl->gmin[1], kInf);
   }
   if (P.inject_wait && blockIdx.x == 0 && threadIdx.x == 0) injected_wait(ctl, P.cap_ns);
@@ -129,38 +142,47 @@ __global__ void __launch_bounds__(1024) kcore_kernel(KcParams P) {
   // CTA-contiguous word ranges for the vertex passes
   const uint32_t per = (nwords + gridDim.x - 1) / gridDim.x;
   const uint32_t wlo = min(nwords, blockIdx.x * per), whi = min(nwords, wlo + per);
+  // Counter slots.  fr[sub % 3] is zero at the top of each bucket; every
+  // phase zeroes the slot after its own, read by nobody since two barriers.
+  // gmin[it % 3] holds bucket it's k at its top; bucket it gathers the next
+  // k in gmin[(it + 1) % 3] and zeroes gmin[(it + 2) % 3] for the one after.
   int bem = 0, sub = 0, tr = 0;  // tr: trace records (bucket passes and peeling rounds)
   for (int it = 0; ok; it++) {
-    // ---------------- NextBucket: smallest D over unfinished vertices
-    if (blockIdx.x == 0 && threadIdx.x == 0) st_vol(ctl->gmin[(it + 1) & 1], kInf);
-    int lm = kInf;
-    for (uint32_t wi = wlo + warp; wi < whi; wi += nw) {
-      const uint32_t v = wi * 32 + lane;
-      const bool un = v < n && !((P.fin[wi] >> lane) & 1u);
-      if (un) lm = min(lm, __ldcg(P.D + v));
-    }
-    const int bm = block_min_i32(lm, s_min);
-    if (threadIdx.x == 0 && bm < kInf) atomicMin(&ctl->gmin[it & 1], bm);
-    if (!grid_sync(ctl, bar, &s_flag)) break;
-    const int32_t k = ld_vol(ctl->gmin[it & 1]);
+    // ---------------- NextBucket: the smallest D over unfinished vertices,
+    // gathered during the previous bucket (its pass and its decrements)
+    const int32_t k = ld_vol(ctl->gmin[it % 3]);
     if (k >= kInf) break;
-    // ---------------- the bucket: unfinished vertices with D <= k
-    if (blockIdx.x == 0 && threadIdx.x == 0) st_vol(ctl->fr[sub % 3], 0ull);
-    if (!grid_sync(ctl, bar, &s_flag)) break;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      st_vol(ctl->gmin[(it + 2) % 3], kInf);
+      st_vol(ctl->fr[(sub + 1) % 3], 0ull);
+    }
+    // ---------------- the bucket: unfinished vertices with D <= k; the
+    // others give the next bucket's candidate minimum
+    int lm = kInf;
     {
       QueueOut out{P.q[0], P.qoff[0], P.qadj[0], P.cs[0], &ctl->fr[sub % 3], n, P.cs_cap};
       constexpr int R = 2 * kU;
       for (uint32_t base = wlo; base < whi; base += R * nw) {
+        uint32_t fw[R];
+        int32_t dv[R];
+#pragma unroll
+        for (int r = 0; r < R; r++) {  // all loads first
+          const uint32_t wi = base + warp + r * nw;
+          const uint32_t v = wi * 32 + lane;
+          fw[r] = wi < whi ? __ldcg(P.fin + wi) : ~0u;
+          dv[r] = (wi < whi && v < n) ? __ldcg(P.D + v) : kInf;
+        }
         uint32_t a[R], z[R];
         bool take[R];
 #pragma unroll
         for (int r = 0; r < R; r++) {
           const uint32_t wi = base + warp + r * nw;
           const uint32_t v = wi * 32 + lane;
-          const uint32_t fw = wi < whi ? P.fin[wi] : ~0u;
-          take[r] = v < n && !((fw >> lane) & 1u) && __ldcg(P.D + v) <= k;
+          const bool un = v < n && !((fw[r] >> lane) & 1u);
+          take[r] = un && dv[r] <= k;
+          if (un && dv[r] > k) lm = min(lm, dv[r]);
           const unsigned tb = __ballot_sync(kFull, take[r]);
-          if (lane == 0 && tb) P.fin[wi] = fw | tb;  // the CTA owns these words here
+          if (lane == 0 && tb) P.fin[wi] = fw[r] | tb;  // the CTA owns these words here
           a[r] = z[r] = 0;
           if (take[r]) {
             P.core[v] = k;
@@ -178,6 +200,10 @@ __global__ void __launch_bounds__(1024) kcore_kernel(KcParams P) {
         stage_make_room(S, out, ctl, R * blockDim.x);
       }
       stage_flush(S, out, ctl);
+    }
+    {
+      const int bm = block_min_i32(lm, s_min);
+      if (threadIdx.x == 0 && bm < ld_vol(ctl->gmin[(it + 1) % 3])) atomicMin(&ctl->gmin[(it + 1) % 3], bm);
     }
     if (!grid_sync(ctl, bar, &s_flag)) break;
     // ---------------- peeling rounds within bucket k
@@ -202,7 +228,7 @@ __global__ void __launch_bounds__(1024) kcore_kernel(KcParams P) {
         scanned += Dsum;
       }
       QueueIn in{P.q[qb], P.qoff[qb], P.qadj[qb], P.cs[qb], cnt, Dsum};
-      PeelFn fn{g.off, g.tgt, P.D, P.core, P.fin, k, 0};
+      PeelFn fn{g.off, g.tgt, P.D, P.core, P.fin, k, 0, kInf};
       StagedSink sink{QueueOut{P.q[qb ^ 1], P.qoff[qb ^ 1], P.qadj[qb ^ 1], P.cs[qb ^ 1], outc, n,
                                P.cs_cap},
                       ctl, nullptr};
@@ -210,6 +236,11 @@ __global__ void __launch_bounds__(1024) kcore_kernel(KcParams P) {
                        (uint32_t)P.bmax, S, fn, sink, ctl, bem++);
       sink.finish(S);
       peeled += fn.peeled;
+      {
+        const int bm = block_min_i32(fn.nmin, s_min);
+        if (threadIdx.x == 0 && bm < ld_vol(ctl->gmin[(it + 1) % 3]))
+          atomicMin(&ctl->gmin[(it + 1) % 3], bm);
+      }
       qb ^= 1;
       if (!grid_sync(ctl, bar, &s_flag)) {
         ok = false;
@@ -220,8 +251,7 @@ __global__ void __launch_bounds__(1024) kcore_kernel(KcParams P) {
         P.trace[tr] = TraceRec{tr + 1, 1, cnt, Dsum, (long long)(globaltimer() - t_start), 0};
       tr++;
     }
-    sub++;  // the bucket pass of the next k uses a fresh counter slot
-    if (blockIdx.x == 0 && threadIdx.x == 0) st_vol(ctl->fr[(sub + 1) % 3], 0ull);
+    sub++;  // the next bucket's pass uses the slot zeroed by the last phase
   }
   unsigned long long t;
   t = block_sum64(scanned, S.misc64);
