@@ -184,6 +184,25 @@ gbf_status gbf_wbfs(gbf_graph *g, int32_t src, int32_t *dist, int mem, const gbf
                     void *cuda_stream);
 
 /*
+ * gbf_delta_stepping — the same shortest paths by Δ-stepping, the bucket
+ * coarsening the SSSP discussion of §7 compares wBFS with (Meyer and Sanders):
+ * bucket q holds the distances [qΔ, (q+1)Δ); a vertex lowered into the bucket
+ * being processed is expanded again in a further round of that bucket (at
+ * most once per round: a test-and-set side list) until the bucket settles,
+ * then the next non-empty bucket is taken.  Distances are exact for every Δ;
+ * Δ trades rounds (grid barriers) against re-expansions.  delta = 1 is gbf_wbfs.
+ *   delta   power of two in [1, 2^20]
+ *   dist    int32[n]: shortest-path distance, GBF_INF if unreachable
+ *   mem     GBF_HOST: blocks; GBF_DEVICE: stream-ordered, see gbf_wait
+ * Errors: as gbf_wbfs; GBF_ERR_INVALID for a bad delta; GBF_ERR_OVERFLOW if a
+ * bucket ring or the overflow bucket ran out of room (possible only on
+ * adversarial inputs; outputs are then undefined).  The dense switch
+ * (dense_wbfs) does not apply.
+ */
+gbf_status gbf_delta_stepping(gbf_graph *g, int32_t src, int32_t delta, int32_t *dist, int mem,
+                              const gbf_options *opt, void *cuda_stream);
+
+/*
  * gbf_bellman_ford — general-weight single-source shortest paths by the
  * frontier Bellman-Ford of §4 "General-Weight SSSP (Bellman-Ford)" (Alg. 4):
  * rounds of the blocked sparse edgeMap whose Update relaxes D[s] + w with

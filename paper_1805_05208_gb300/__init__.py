@@ -100,6 +100,7 @@ def _load() -> ctypes.CDLL:
         "gbf_graph_device_bytes": (S, [P, ctypes.POINTER(ctypes.c_size_t)]),
         "gbf_bfs": (S, [P, I32, P, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
         "gbf_wbfs": (S, [P, I32, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
+        "gbf_delta_stepping": (S, [P, I32, I32, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
         "gbf_bellman_ford": (S, [P, I32, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
         "gbf_widest_path": (S, [P, I32, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
         "gbf_betweenness": (S, [P, I32, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
@@ -224,6 +225,14 @@ def gbf_wbfs(h: int, src: int, dist, opt: Optional[gbf_options] = None, stream=N
     """Integral-weight SSSP from src into dist."""
     pd, mem = _ptr(dist)
     _check(_lib.gbf_wbfs(h, int(src), pd, mem, _opt(opt), _stream(stream)), "gbf_wbfs")
+
+
+def gbf_delta_stepping(h: int, src: int, delta: int, dist, opt: Optional[gbf_options] = None,
+                       stream=None) -> None:
+    """Integral-weight SSSP from src into dist by Δ-stepping (delta a power of two)."""
+    pd, mem = _ptr(dist)
+    _check(_lib.gbf_delta_stepping(h, int(src), int(delta), pd, mem, _opt(opt), _stream(stream)),
+           "gbf_delta_stepping")
 
 
 def gbf_bellman_ford(h: int, src: int, dist, opt: Optional[gbf_options] = None,
@@ -409,6 +418,11 @@ class Graph:
     def wbfs(self, src: int, opt=None):
         d = np.empty(self.n, dtype=np.int32)
         gbf_wbfs(self.h, src, d, opt)
+        return d
+
+    def delta_stepping(self, src: int, delta: int, opt=None):
+        d = np.empty(self.n, dtype=np.int32)
+        gbf_delta_stepping(self.h, src, delta, d, opt)
         return d
 
     def bellman_ford(self, src: int, opt=None):

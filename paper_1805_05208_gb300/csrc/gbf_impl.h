@@ -35,6 +35,7 @@ struct Ctl {
   // wBFS
   unsigned int mcnt[2];        // moved-list counts, by round parity
   int gmin[3];                 // k-core: smallest remaining degree of the next bucket, by bucket % 3
+  unsigned int scnt[3];        // Δ-stepping: side-list counts, by round % 3
   unsigned int ovf_cnt[2];     // overflow bucket counts
   int ovf_min[2];              // overflow bucket minimum value
   unsigned int imask[3][32];   // buckets filed into during round t, by t % 3 (one bit per slot)
@@ -91,6 +92,8 @@ struct Workspace {
   int32_t nB = 0;
   int2 *ovf[2] = {nullptr, nullptr};
   uint64_t ovf_cap = 0;
+  int32_t *side[2] = {nullptr, nullptr};  // Δ-stepping side lists (lazy), n each
+  int32_t *xround = nullptr;               // Δ-stepping: last round each vertex was expanded
   // MS-BFS (lazy); queues 0 and 1 are shared with q/qoff/cs above
   unsigned long long *ms_seen = nullptr, *ms_visit = nullptr, *ms_next = nullptr;
   int32_t *ms_q[3] = {nullptr, nullptr, nullptr};
@@ -151,7 +154,7 @@ gbf_status check_smem(size_t bytes, const char *kernel);
 
 // Workspace management (graph.cu)
 gbf_status ws_ensure_base(Graph &g, Workspace &ws);
-gbf_status ws_ensure_wbfs(Graph &g, Workspace &ws, int nB);
+gbf_status ws_ensure_wbfs(Graph &g, Workspace &ws, int nB, int dl = 0);
 gbf_status ws_ensure_msbfs(Graph &g, Workspace &ws, bool host_out);
 gbf_status ws_ensure_bc(Graph &g, Workspace &ws);
 void ws_free(Workspace &ws);
@@ -160,8 +163,9 @@ gbf_status ws_collect(Workspace &ws, cudaStream_t st, gbf_stats *stats);
 // Launchers (bfs.cu / wbfs.cu / msbfs.cu); outputs are device pointers.
 gbf_status launch_bfs(Graph &g, Workspace &ws, int32_t src, int32_t *dist, int32_t *parent,
                       const Opts &o, cudaStream_t st);
+// dl > 0: Δ-stepping with Δ = 2^dl (needs ws_ensure_wbfs(..., dl) side lists)
 gbf_status launch_wbfs(Graph &g, Workspace &ws, int32_t src, int32_t *dist, const Opts &o,
-                       cudaStream_t st);
+                       cudaStream_t st, int dl = 0);
 gbf_status launch_msbfs(Graph &g, Workspace &ws, const int32_t *srcs_host, int32_t k,
                         int32_t *dist, const Opts &o, cudaStream_t st);
 // Resident CTAs per SM of each persistent kernel for these knobs (0 on error).

@@ -220,7 +220,7 @@ gbf_status ws_ensure_base(Graph &g, Workspace &ws) {
   return GBF_OK;
 }
 
-gbf_status ws_ensure_wbfs(Graph &g, Workspace &ws, int nB) {
+gbf_status ws_ensure_wbfs(Graph &g, Workspace &ws, int nB, int dl) {
   GBF_TRY(ws_ensure_base(g, ws));
   const size_t n = (size_t)g.n;
   size_t acc = 0;
@@ -238,9 +238,17 @@ gbf_status ws_ensure_wbfs(Graph &g, Workspace &ws, int nB) {
     ws.nB = nB;
   }
   // The overflow bucket is only reachable when the window is narrower than
-  // the weight range; each live (vertex, value) pair is filed at most once,
-  // bounded by the number of successful relaxations (<= m) plus n.
-  const bool need_ovf = (uint32_t)nB <= g.w_max;
+  // the largest bucket step of one relaxation; each live (vertex, value) pair
+  // is filed at most once, bounded by the number of successful relaxations
+  // (<= m in exact wBFS) plus n.  Δ-stepping can exceed it on adversarial
+  // inputs; the kernel then reports GBF_ERR_OVERFLOW.
+  const uint32_t jump = (((1u << dl) - 1u) + g.w_max) >> dl;
+  const bool need_ovf = (uint32_t)nB <= jump;
+  if (dl > 0 && !ws.side[0]) {
+    GBF_TRY(dmalloc(&ws.side[0], n, acc));
+    GBF_TRY(dmalloc(&ws.side[1], n, acc));
+    GBF_TRY(dmalloc(&ws.xround, n, acc));
+  }
   const uint64_t cap = need_ovf ? (uint64_t)g.m + n : 1;
   if (ws.ovf_cap < cap) {
     for (int i = 0; i < 2; i++)
@@ -314,7 +322,7 @@ void ws_free(Workspace &ws) {
                   ws.slot_cnt, ws.ovf[0], ws.ovf[1], ws.ms_seen, ws.ms_visit, ws.ms_next,
                   ws.ms_q[2], ws.ms_qoff[2], ws.ms_cs[2], ws.ms_touched, ws.ms_call,
                   ws.ms_dist_tmp, ws.bc_paths, ws.bc_lvl, ws.bc_cs, ws.bc_info,
-                  ws.bc_out_tmp};
+                  ws.bc_out_tmp, ws.side[0], ws.side[1], ws.xround};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (ws.ctl_host) cudaFreeHost(ws.ctl_host);
@@ -549,6 +557,32 @@ gbf_status gbf_wbfs(gbf_graph *h, int32_t src, int32_t *dist, int mem, const gbf
   GBF_TRY(ws_ensure_wbfs(g, g.ws, nB));
   int32_t *dd = mem == GBF_HOST ? g.ws.dist_tmp : dist;
   GBF_TRY(launch_wbfs(g, g.ws, src, dd, o, st));
+  if (mem == GBF_DEVICE) return GBF_OK;
+  GBF_CUDA(cudaMemcpyAsync(dist, dd, sizeof(int32_t) * (size_t)g.n, cudaMemcpyDeviceToHost, st));
+  return ws_collect(g.ws, st, nullptr);
+}
+
+gbf_status gbf_delta_stepping(gbf_graph *h, int32_t src, int32_t delta, int32_t *dist, int mem,
+                              const gbf_options *opt, void *cuda_stream) {
+  if (!h || !dist) return set_error("graph or dist is NULL"), GBF_ERR_INVALID;
+  Graph &g = h->g;
+  if (!g.w) return set_error("graph has no weights"), GBF_ERR_INVALID;
+  if (src < 0 || src >= g.n) return set_error("src out of range"), GBF_ERR_INVALID;
+  if (mem != GBF_HOST && mem != GBF_DEVICE) return set_error("bad mem"), GBF_ERR_INVALID;
+  int dl = 0;
+  while (dl <= 20 && (1 << dl) < delta) dl++;
+  if (delta < 1 || dl > 20 || (1 << dl) != delta)
+    return set_error("delta must be a power of two in [1, 2^20]"), GBF_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  std::lock_guard<std::mutex> lk(g.mu);
+  const Opts o = resolve(opt, g, GBF_TUNE_WBFS);
+  // a window one wider than the largest bucket step slides without overflow
+  const uint32_t jump = (((1u << dl) - 1u) + g.w_max) >> dl;
+  int nB = o.bucket_window > 0 ? o.bucket_window : (int)std::max<uint32_t>(jump + 1, 2);
+  nB = std::min(nB, 256);
+  GBF_TRY(ws_ensure_wbfs(g, g.ws, nB, dl));
+  int32_t *dd = mem == GBF_HOST ? g.ws.dist_tmp : dist;
+  GBF_TRY(launch_wbfs(g, g.ws, src, dd, o, st, dl));
   if (mem == GBF_DEVICE) return GBF_OK;
   GBF_CUDA(cudaMemcpyAsync(dist, dd, sizeof(int32_t) * (size_t)g.n, cudaMemcpyDeviceToHost, st));
   return ws_collect(g.ws, st, nullptr);

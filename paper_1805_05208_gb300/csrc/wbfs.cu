@@ -10,10 +10,13 @@
 //     the bucket of its new distance (Reset + updateBuckets of Alg. 3, done
 //     at the write instead of in a later vertexMap pass, so a round needs no
 //     Moved list and no test-and-set: a vertex lowered twice in a round
-//     leaves one stale entry behind).
-//       - vertices of degree <= heavy_cutoff / 8 are expanded by their warp: the warp's
-//         32 entries get a warp-local degree prefix and the warp walks their
-//         arcs 32 at a time (every lane busy, coalesced target loads);
+//     leaves one stale entry behind).  A vertex of degree 1 is not filed:
+//     lowered through its only neighbour, it has its final distance and
+//     nothing to relax.
+//       - vertices with at most heavy_cutoff / 8 arcs (32 at least) are
+//         expanded by the CTA that extracted them: a CTA-local degree prefix
+//         over the staged entries, then warps walk their arcs in 32-arc
+//         windows (the blocked edgeMap's walk, on one CTA's entries);
 //       - heavier vertices are compacted into a frontier queue with a global
 //         degree prefix and expanded afterwards by the blocked edgeMap
 //         (§6.2) over all CTAs, so one hub is spread over the whole GPU.
@@ -32,6 +35,16 @@
 // to the current bucket and nothing overflows.  Otherwise the window is fixed
 // and values beyond it go to an overflow bucket, which refills a window
 // starting at its minimum once the open buckets run dry.
+//
+// Δ-stepping (the coarsening the SSSP discussion of §7 sets wBFS against;
+// the kDelta instance, Δ = 2^dl): bucket q holds the distances [qΔ, (q+1)Δ)
+// and "value" above reads "bucket index" (an entry is live iff D[v] / Δ is
+// its bucket).  Each arc adds w to its source's current D.  A vertex lowered
+// into the bucket being processed goes on the round's side list (a
+// test-and-set on a per-round flag bitmap keeps it there once) and the next
+// round expands the side list, again in bucket b, until a round leaves it
+// empty; only then is the next bucket taken.  Distances are exact for any Δ:
+// every vertex is expanded again after its last lowering.
 #include <cuda_runtime.h>
 
 #include "dev_common.cuh"
@@ -66,6 +79,13 @@ struct WbfsParams {
   int heavy;
   int inject_wait;
   long long cap_ns;
+  // Δ-stepping (dl > 0): buckets hold distance ranges [qΔ, (q+1)Δ), Δ = 2^dl;
+  // a vertex lowered into the bucket being processed joins that round's side
+  // list (once per round: test-and-set on a flag bitmap) instead of a ring
+  int dl;
+  int32_t *side[2];   // side lists by round parity, n entries each
+  uint32_t *sflag[2]; // their flag bitmaps, ceil(n/32) words each
+  int32_t *xround;    // the last round each vertex was expanded in (n)
 };
 
 namespace {
@@ -88,6 +108,10 @@ struct FileSink {
   Counters *c;
   unsigned *imask;   // this round's filed-slot mask (global)
   unsigned *s_pub;   // slots this CTA already published this round
+  int32_t bq;        // bucket being processed (Δ-stepping), -1 if none
+  int32_t *sq;       // this round's side list, its flag bitmap and count
+  uint32_t *sfl;
+  unsigned *scnt;
 
   __device__ __forceinline__ void append(PushSmem &S, bool low, int32_t v, uint32_t ndu) {
     const unsigned bal = __ballot_sync(kFull, low);
@@ -98,45 +122,41 @@ struct FileSink {
     if (lane == leader) pos = atomicAdd(&S.misc[4], (uint32_t)__popc(bal));
     pos = __shfl_sync(kFull, pos, leader);
     if (!low) return;
-    const int32_t nd = (int32_t)ndu;
-    const int32_t sl = (P->slide || nd < lo + P->nB) ? nd % P->nB : -nd - 2;
+    const int32_t sl = slot_of((int32_t)ndu);
     const uint32_t r = pos + __popc(bal & lanemask_lt());
     if (r < S.cap_out) {
       S.fv[r] = v;
       S.fs[r] = sl;
       return;
     }
-    // the stage is full: file this entry directly
-    if (sl >= 0) {
-      const uint32_t gp = atomicAdd(P->slot_cnt + sl, 1u) % (uint32_t)P->g.n;
-      P->slots[(size_t)sl * (size_t)P->g.n + gp] = v;
-      atomicOr(imask + (sl >> 5), 1u << (sl & 31));
-    } else {
-      const uint32_t gp = atomicAdd(&P->ctl->ovf_cnt[cur], 1u);
-      if (gp < P->ovf_cap) {
-        P->ovf[cur][gp] = make_int2(v, nd);
-        atomicMin(&P->ctl->ovf_min[cur], nd);
-      } else {
-        raise_error(P->ctl, GBF_ERR_OVERFLOW, 12);
-      }
-    }
-    c->inserts++;
+    file_direct(v, (int32_t)ndu, sl);  // the stage is full
   }
-  // The bucket slot of value nd (or -nd - 2: the overflow bucket).
+  // Where distance nd is filed: ring slot q mod nB of its bucket q, the
+  // overflow bucket (-q - 2) beyond a fixed window, or nB: the side list of
+  // the bucket being processed (Δ-stepping only; in exact wBFS every filed
+  // distance lies above the current bucket).
   __device__ __forceinline__ int32_t slot_of(int32_t nd) const {
-    return (P->slide || nd < lo + P->nB) ? nd % P->nB : -nd - 2;
+    const int32_t q = nd >> P->dl;
+    if (q == bq) return P->nB;
+    return (P->slide || q < lo + P->nB) ? q % P->nB : -q - 2;
   }
   // An entry that found the stage full, filed directly.
   __device__ __forceinline__ void file_direct(int32_t v, int32_t nd, int32_t sl) {
-    if (sl >= 0) {
+    if (sl == P->nB) {
+      const unsigned bit = 1u << (v & 31);
+      if (atomicOr(sfl + (v >> 5), bit) & bit) return;  // already on this round's side list
+      const uint32_t gp = atomicAdd(scnt, 1u);
+      if (gp < (uint32_t)P->g.n) sq[gp] = v;
+      else raise_error(P->ctl, GBF_ERR_OVERFLOW, 13);
+    } else if (sl >= 0) {
       const uint32_t gp = atomicAdd(P->slot_cnt + sl, 1u) % (uint32_t)P->g.n;
       P->slots[(size_t)sl * (size_t)P->g.n + gp] = v;
       atomicOr(imask + (sl >> 5), 1u << (sl & 31));
     } else {
       const uint32_t gp = atomicAdd(&P->ctl->ovf_cnt[cur], 1u);
       if (gp < P->ovf_cap) {
-        P->ovf[cur][gp] = make_int2(v, nd);
-        atomicMin(&P->ctl->ovf_min[cur], nd);
+        P->ovf[cur][gp] = make_int2(v, -sl - 2);
+        atomicMin(&P->ctl->ovf_min[cur], -sl - 2);
       } else {
         raise_error(P->ctl, GBF_ERR_OVERFLOW, 12);
       }
@@ -189,7 +209,7 @@ struct FileSink {
     if (k == 0) return;
     const int nB = P->nB;
     const uint32_t n = (uint32_t)P->g.n;
-    for (int i = threadIdx.x; i < nB; i += blockDim.x) S.hist[i] = 0u;
+    for (int i = threadIdx.x; i <= nB; i += blockDim.x) S.hist[i] = 0u;  // [nB]: side list
     if (threadIdx.x == 0) {
       S.misc[5] = 0u;
       S.misc[7] = (uint32_t)kInf;
@@ -206,7 +226,14 @@ struct FileSink {
         continue;
       }
       const int32_t sl = S.fs[i];
-      if (sl >= 0) {
+      if (sl == nB) {  // side list: once per vertex and round
+        const unsigned bit = 1u << (v & 31);
+        if (atomicOr(sfl + (v >> 5), bit) & bit) {
+          S.fs[i] = kNoSlot;
+          continue;
+        }
+        S.pref[i] = atomicAdd(&S.hist[nB], 1u);
+      } else if (sl >= 0) {
         S.pref[i] = atomicAdd(&S.hist[sl], 1u);
       } else {
         S.pref[i] = atomicAdd(&S.misc[5], 1u);
@@ -214,6 +241,7 @@ struct FileSink {
       }
     }
     __syncthreads();
+    if (threadIdx.x == 0 && S.hist[nB]) S.gbase[nB] = atomicAdd(scnt, S.hist[nB]);
     for (int i = threadIdx.x; i < nB; i += blockDim.x) {
       const uint32_t h = S.hist[i];
       if (h) {
@@ -234,7 +262,12 @@ struct FileSink {
       const int32_t sl = S.fs[i];
       const int32_t v = S.fv[i];
       if (sl == kNoSlot) continue;
-      if (sl >= 0) {
+      if (sl == nB) {
+        const uint32_t pos = S.gbase[nB] + S.pref[i];
+        if (pos < n) sq[pos] = v;
+        else raise_error(P->ctl, GBF_ERR_OVERFLOW, 14);
+        c->inserts++;
+      } else if (sl >= 0) {
         const uint32_t pos = (S.gbase[sl] + S.pref[i]) % n;
         P->slots[(size_t)sl * n + pos] = v;
         c->inserts++;
@@ -255,7 +288,10 @@ struct FileSink {
 // weight loads, then the distance loads, then the writeMins.  The writeMins
 // of a step are consumed (successes filed) at the next step, after its
 // target loads are issued, so their latency overlaps the next step's loads;
-// drain() files the last step's.
+// drain() files the last step's.  In exact wBFS every live entry of bucket b
+// has D == b, so nDist = b + w; under Δ-stepping (kDelta) the bucket holds a
+// range of distances and each arc adds w to its source's current D.
+template <bool kDelta>
 struct RelaxFn {
   static constexpr int kWin = kU;  // windows per walk step
   const int32_t *tgt;
@@ -281,13 +317,14 @@ struct RelaxFn {
     for (int r = 0; r < kU; r++) pold[r] = pnd[r];
   }
   template <class Sink>
-  __device__ __forceinline__ void batch(const bool *val, const int32_t *, const uint32_t *idx,
+  __device__ __forceinline__ void batch(const bool *val, const int32_t *uu, const uint32_t *idx,
                                         Sink &sink, PushSmem &S) {
     int32_t v[kU], nd[kU];
 #pragma unroll
     for (int r = 0; r < kU; r++) {
+      const int32_t base = kDelta ? (val[r] ? __ldcg(dist + uu[r]) : 0) : b;
       v[r] = val[r] ? (int32_t)ldg_pol(tgt + idx[r], stream_pol) : 0;
-      nd[r] = val[r] ? b + (int32_t)ldg_pol(w + idx[r], stream_pol) : kInf;
+      nd[r] = val[r] ? base + (int32_t)ldg_pol(w + idx[r], stream_pol) : kInf;
     }
     drain(sink, S);
     // read D at L2 (.cg): L1 lines of D go stale as other SMs lower it, and a
@@ -381,6 +418,13 @@ __device__ int32_t next_bucket(const unsigned *s_pend, int nB, int32_t lo, int *
 
 }  // namespace
 
+// Shared-memory shape of the kernel: the filing histogram has nB ring slots
+// and the side list.
+__host__ __device__ inline SmemShape wbfs_smem_shape(int bmax, int cap, int nB) {
+  return SmemShape{bmax, cap, 1, nB + 1};
+}
+
+template <bool kDelta>
 __global__ void __launch_bounds__(1024) wbfs_kernel(WbfsParams P) {
   extern __shared__ unsigned long long smem_raw[];
   __shared__ int s_flag;
@@ -388,7 +432,7 @@ __global__ void __launch_bounds__(1024) wbfs_kernel(WbfsParams P) {
   __shared__ unsigned s_pend[kMaskWords];  // slots with unconsumed entries
   __shared__ unsigned s_pub[kMaskWords];   // slots this CTA already published this round
   const int nB = P.nB;
-  const SmemShape sh{P.bmax, P.cap, 1, nB};
+  const SmemShape sh = wbfs_smem_shape(P.bmax, P.cap, nB);
   PushSmem S = carve_push_smem(smem_raw, sh);
   uint32_t *s_base = (uint32_t *)((char *)smem_raw + push_smem_bytes(sh));
   for (int i = threadIdx.x; i < nB; i += blockDim.x) s_base[i] = 0u;
@@ -410,6 +454,14 @@ __global__ void __launch_bounds__(1024) wbfs_kernel(WbfsParams P) {
 
   // makeBuckets: D = inf except D[src] = 0; src filed in bucket 0.
   for (uint32_t i = gt; i < (uint32_t)g.n; i += gs) P.dist[i] = (i == (uint32_t)src) ? 0 : kInf;
+  if (kDelta) {
+    const uint32_t nwords = ((uint32_t)g.n + 31) >> 5;
+    for (uint32_t i = gt; i < nwords; i += gs) {
+      P.sflag[0][i] = 0u;
+      P.sflag[1][i] = 0u;
+    }
+    for (uint32_t i = gt; i < (uint32_t)g.n; i += gs) P.xround[i] = 0;
+  }
   if (blockIdx.x == 0) {
     for (int i = threadIdx.x; i < nB; i += blockDim.x) P.slot_cnt[i] = (i == 0) ? 1u : 0u;
     if (threadIdx.x == 0) {
@@ -426,6 +478,7 @@ __global__ void __launch_bounds__(1024) wbfs_kernel(WbfsParams P) {
   int bem = 0;         // blocked edgeMap invocations so far
   int cur = 0;         // active overflow buffer
   int32_t prev = -1;   // slot consumed by the previous round (-1: none)
+  int32_t bcur = -1;   // Δ-stepping: the bucket being processed
   for (int32_t t = 1; ok; t++) {
     // ---------------- nextBucket.  Pending slots: those of the last round
     // minus the one it consumed, plus every slot filed into during it (the
@@ -442,7 +495,17 @@ __global__ void __launch_bounds__(1024) wbfs_kernel(WbfsParams P) {
     __syncthreads();
     if (blockIdx.x == 0 && threadIdx.x < kMaskWords) st_vol(ctl->imask[(t + 1) % 3][threadIdx.x], 0u);
     if (blockIdx.x == 0 && threadIdx.x == 0) st_vol(ctl->fr[(t + 1) % 3], 0ull);
-    const int32_t b = next_bucket(s_pend, nB, lo, s_int);
+    // Δ-stepping: vertices lowered into the current bucket during round t-1
+    // (its side list, complete at the barrier) are expanded again before the
+    // bucket is left.  Counter slots by t % 3: this round files into t % 3,
+    // and (t + 1) % 3 was last read at the top of round t - 1.
+    uint32_t side_cnt = 0;
+    if (kDelta) {
+      side_cnt = min(ld_vol(ctl->scnt[(t + 2) % 3]), (uint32_t)g.n);
+      if (blockIdx.x == 0 && threadIdx.x == 0) st_vol(ctl->scnt[(t + 1) % 3], 0u);
+    }
+    const bool side_round = kDelta && side_cnt > 0;
+    const int32_t b = side_round ? bcur : next_bucket(s_pend, nB, lo, s_int);
     if (b == kInf) {
       // open buckets are dry: refill from the overflow bucket, or finish
       const uint32_t oc = min(ld_vol(ctl->ovf_cnt[cur]), P.ovf_cap);
@@ -450,13 +513,13 @@ __global__ void __launch_bounds__(1024) wbfs_kernel(WbfsParams P) {
       const int32_t nlo = ld_vol(ctl->ovf_min[cur]);
       if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&ctl->refills, 1);
       // into the new window [nlo, nlo + nB), the rest into the other buffer
-      FileSink fs{&P, nlo, cur ^ 1, &c, imask, s_pub};
+      FileSink fs{&P, nlo, cur ^ 1, &c, imask, s_pub, -1, nullptr, nullptr, nullptr};
       for (uint32_t base = blockIdx.x * blockDim.x; base < oc; base += gs) {
         const uint32_t i = base + threadIdx.x;
         const bool valid = i < oc;
-        const int2 e = valid ? P.ovf[cur][i] : make_int2(0, 0);
-        const bool live = valid && P.dist[e.x] == e.y;
-        fs.append(S, live, e.x, (uint32_t)e.y);
+        const int2 e = valid ? P.ovf[cur][i] : make_int2(0, 0);  // (vertex, bucket)
+        const bool live = valid && (P.dist[e.x] >> P.dl) == e.y;
+        fs.append(S, live, e.x, (uint32_t)e.y << P.dl);
         fs.chunk_end(S);
       }
       fs.flush(S);
@@ -472,20 +535,36 @@ __global__ void __launch_bounds__(1024) wbfs_kernel(WbfsParams P) {
       if (!grid_sync(ctl, bar, &s_flag)) break;
       continue;
     }
-    if (P.slide) lo = b;
-    const int sb = b % nB;
-    prev = sb;
-    // No CTA files into slot sb during this round (its values differ from b
-    // by less than nB), so its counter is stable here.
-    const uint32_t rb = s_base[sb];
-    const uint32_t cntb = min(ld_vol(P.slot_cnt[sb]) - rb, (uint32_t)g.n);
-    __syncthreads();
-    if (threadIdx.x == 0) s_base[sb] = rb + cntb;
-    __syncthreads();
+    // The entries of this round: bucket b's ring slot, or (Δ-stepping) the
+    // side list of round t-1.
+    uint32_t rb = 0, cntb = side_cnt;
+    const int32_t *elist;
+    if (side_round) {
+      prev = -1;
+      elist = P.side[(t + 1) & 1];
+    } else {
+      if (P.slide) lo = b;
+      const int sb = b % nB;
+      prev = sb;
+      bcur = b;
+      // No CTA files into slot sb during this round (exact wBFS files values
+      // above b, less than nB above; Δ-stepping files bucket b into the side
+      // list), so its counter is stable here.
+      rb = s_base[sb];
+      const uint32_t avail = ld_vol(P.slot_cnt[sb]) - rb;
+      if (avail > (uint32_t)g.n && blockIdx.x == 0 && threadIdx.x == 0)
+        raise_error(ctl, GBF_ERR_OVERFLOW, 15);  // a ring wrapped over unconsumed entries
+      cntb = min(avail, (uint32_t)g.n);
+      __syncthreads();
+      if (threadIdx.x == 0) s_base[sb] = rb + cntb;
+      __syncthreads();
+      elist = P.slots + (size_t)sb * (size_t)g.n;
+    }
     unsigned long long *fctr = &ctl->fr[t % 3];
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&ctl->rounds, 1);
-    FileSink fsink{&P, lo, cur, &c, imask, s_pub};
-    const bool dense = P.dense && P.pull_divisor > 0 &&
+    FileSink fsink{&P, lo, cur, &c, imask, s_pub, kDelta ? b : -1, P.side[t & 1], P.sflag[t & 1],
+                   &ctl->scnt[t % 3]};
+    const bool dense = !kDelta && P.dense && P.pull_divisor > 0 &&
                        (unsigned long long)cntb * (unsigned)P.pull_divisor > (unsigned long long)g.n;
     if (dense) {
       if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&ctl->pull_rounds, 1);
@@ -498,18 +577,21 @@ __global__ void __launch_bounds__(1024) wbfs_kernel(WbfsParams P) {
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&ctl->push_rounds, 1);
     // ---------------- edgeMapData over the live entries of bucket b
     QueueOut fout{P.q, P.qoff, nullptr, P.cs, fctr, (uint32_t)g.n, P.cs_cap};
-    RelaxFn fn{g.tgt, g.w, P.dist, b, 0};
+    RelaxFn<kDelta> fn{g.tgt, g.w, P.dist, b, 0};
     fn.stream_pol = l2_evict_first();
     fn.keep_pol = l2_evict_last();
-    const int32_t *sl = P.slots + (size_t)sb * (size_t)g.n;
     for (uint32_t it = blockIdx.x * blockDim.x; it < cntb; it += gs) {
       const uint32_t i = it + threadIdx.x;
       int32_t v = 0;
       bool live = false;
       uint32_t a0 = 0, deg = 0;
       if (i < cntb) {
-        v = sl[(rb + i) % (uint32_t)g.n];
-        if (P.dist[v] == b) {
+        v = elist[side_round ? i : (rb + i) % (uint32_t)g.n];
+        if (side_round) atomicAnd(P.sflag[(t + 1) & 1] + (v >> 5), ~(1u << (v & 31)));
+        // Δ-stepping: a bucket may hold a vertex more than once (lowered
+        // twice inside its range before the bucket came up); it is expanded
+        // once per round, which also bounds a round's arcs by m
+        if ((P.dist[v] >> P.dl) == b && (!kDelta || atomicExch(P.xround + v, t) != t)) {
           a0 = __ldg(g.off + v);
           deg = __ldg(g.off + v + 1) - a0;
           // a degree-1 vertex other than the source was reached from its only
@@ -549,7 +631,11 @@ __global__ void __launch_bounds__(1024) wbfs_kernel(WbfsParams P) {
     const unsigned long long fr = ld_vol(*fctr);
     const uint32_t hcnt = (uint32_t)(fr >> 32), hD = (uint32_t)fr;
     const long long t_mid = (long long)(globaltimer() - t_start);
-    if (hcnt > 0) {
+    if (hcnt > 0 && ((uint64_t)hD + kFine - 1) / kFine > P.cs_cap) {
+      // more arcs than the chunk-start table covers (a round expands every
+      // vertex at most once, so never expected)
+      if (blockIdx.x == 0 && threadIdx.x == 0) raise_error(ctl, GBF_ERR_OVERFLOW, 16);
+    } else if (hcnt > 0) {
       // heavy vertices of the bucket: blocked edgeMap over all CTAs
       QueueIn in{P.q, P.qoff, nullptr, P.cs, hcnt, hD};
       // every heavy vertex has more than P.heavy edges
@@ -579,8 +665,11 @@ __global__ void __launch_bounds__(1024) wbfs_kernel(WbfsParams P) {
 }
 
 gbf_status launch_wbfs(Graph &g, Workspace &ws, int32_t src, int32_t *dist, const Opts &o,
-                       cudaStream_t st) {
+                       cudaStream_t st, int dl) {
   if (!g.leaf) return set_error("graph has no degree-1 bitmap"), GBF_ERR_INVALID;
+  if (dl < 0 || dl > 20) return set_error("delta must be 2^0 .. 2^20"), GBF_ERR_INVALID;
+  if (dl > 0 && (!ws.side[0] || !ws.side[1] || !ws.xround))
+    return set_error("no side lists"), GBF_ERR_INVALID;
   WbfsParams P;
   P.g = g.dev();
   P.leaf = g.leaf;
@@ -589,7 +678,9 @@ gbf_status launch_wbfs(Graph &g, Workspace &ws, int32_t src, int32_t *dist, cons
   P.slots = ws.slots;
   P.slot_cnt = ws.slot_cnt;
   P.nB = ws.nB;
-  P.slide = (uint32_t)ws.nB > g.w_max ? 1 : 0;
+  // the largest bucket step of one relaxation is floor((Δ - 1 + w_max) / Δ)
+  const uint32_t jump = (((1u << dl) - 1u) + g.w_max) >> dl;
+  P.slide = (uint32_t)ws.nB > jump ? 1 : 0;
   P.ovf[0] = ws.ovf[0];
   P.ovf[1] = ws.ovf[1];
   P.ovf_cap = (uint32_t)ws.ovf_cap;
@@ -601,7 +692,7 @@ gbf_status launch_wbfs(Graph &g, Workspace &ws, int32_t src, int32_t *dist, cons
   P.trace = ws.trace;
   P.trace_cap = ws.trace_cap;
   P.pull_divisor = o.pull_divisor;
-  P.dense = o.dense_wbfs;
+  P.dense = dl == 0 ? o.dense_wbfs : 0;
   P.bmax = o.heavy_cutoff;
   P.cap = stage_capacity(o.block);
   int l = 0;
@@ -611,16 +702,22 @@ gbf_status launch_wbfs(Graph &g, Workspace &ws, int32_t src, int32_t *dist, cons
   P.heavy = o.heavy_cutoff / 8 > 32 ? o.heavy_cutoff / 8 : 32;
   P.inject_wait = o.inject_wait;
   P.cap_ns = o.spin_cap_ns;
+  P.dl = dl;
+  P.side[0] = ws.side[0];
+  P.side[1] = ws.side[1];
+  P.sflag[0] = ws.fbm[0];
+  P.sflag[1] = ws.fbm[1];
+  P.xround = ws.xround;
+  const void *kern = dl > 0 ? (const void *)wbfs_kernel<true> : (const void *)wbfs_kernel<false>;
   const size_t smem =
-      push_smem_bytes(SmemShape{P.bmax, P.cap, 1, ws.nB}) + sizeof(uint32_t) * (size_t)ws.nB;
+      push_smem_bytes(wbfs_smem_shape(P.bmax, P.cap, ws.nB)) + sizeof(uint32_t) * (size_t)ws.nB;
   {
     const gbf_status sm = check_smem(smem, "wbfs_kernel");
     if (sm != GBF_OK) return sm;
   }
-  GBF_CUDA(cudaFuncSetAttribute(wbfs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem));
+  GBF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  GBF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wbfs_kernel, o.block, smem));
+  GBF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, o.block, smem));
   if (per_sm < 1) {
     set_error("wbfs kernel does not fit on an SM with this block size");
     return GBF_ERR_INVALID;
@@ -630,8 +727,7 @@ gbf_status launch_wbfs(Graph &g, Workspace &ws, int32_t src, int32_t *dist, cons
   GBF_CUDA(cudaMemsetAsync(ws.ctl, 0, sizeof(Ctl), st));
   if (ws.trace) GBF_CUDA(cudaMemsetAsync(ws.trace, 0, sizeof(TraceRec) * (size_t)ws.trace_cap, st));
   void *args[] = {&P};
-  GBF_CUDA(cudaLaunchCooperativeKernel((const void *)wbfs_kernel, dim3(grid), dim3(o.block), args,
-                                       smem, st));
+  GBF_CUDA(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(o.block), args, smem, st));
   ws.last_kind = 2;
   ws.last_grid = grid;
   ws.last_block = o.block;
@@ -639,13 +735,14 @@ gbf_status launch_wbfs(Graph &g, Workspace &ws, int32_t src, int32_t *dist, cons
 }
 
 int resident_ctas_per_sm_wbfs(const Opts &o, int nB) {
-  const size_t smem = push_smem_bytes(SmemShape{o.heavy_cutoff, stage_capacity(o.block), 1, nB}) +
+  const size_t smem = push_smem_bytes(wbfs_smem_shape(o.heavy_cutoff, stage_capacity(o.block), nB)) +
                       sizeof(uint32_t) * (size_t)nB;
-  if (cudaFuncSetAttribute(wbfs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-      cudaSuccess)
+  if (cudaFuncSetAttribute(wbfs_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem) != cudaSuccess)
     return 0;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wbfs_kernel, o.block, smem) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wbfs_kernel<false>, o.block, smem) !=
+      cudaSuccess)
     return 0;
   return per_sm;
 }
