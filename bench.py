@@ -74,6 +74,12 @@ WORKLOADS = {
                      desc="BFS, 4096x4096 grid, 10% edges deleted, source 0 + 3 seeded"),
     "wbfs-grid": dict(kind="wbfs", graph="grid", R=4096, C=4096, w=(1, 16), nsrc=4,
                       desc="wBFS, 4096x4096 grid, 10% deleted, w in [1,16), source 0 + 3 seeded"),
+    "delta-grid": dict(kind="delta", delta=64, graph="grid", R=4096, C=4096, w=(1, 16), nsrc=4,
+                       desc="delta-stepping (delta 64), 4096x4096 grid, 10% deleted, w in [1,16), "
+                            "source 0 + 3 seeded"),
+    "delta-rmat22": dict(kind="delta", delta=4, graph="rmat", scale=22, ef=16, w=(1, 22), nsrc=8,
+                         desc="delta-stepping (delta 4), RMAT scale 22 ef16, w in [1,22), "
+                              "8 seeded sources one at a time"),
 }
 
 
@@ -117,7 +123,7 @@ def make_sources(g, wl, rank=0):
     return G.sources(g, k, seed=3 + 1000 * rank)
 
 
-ORACLE_NAME = {"bfs": "FIFO BFS", "wbfs": "binary-heap Dijkstra",
+ORACLE_NAME = {"bfs": "FIFO BFS", "wbfs": "binary-heap Dijkstra", "delta": "binary-heap Dijkstra",
                "bf": "frontier Bellman-Ford", "widest": "(max,min) Bellman-Ford rounds",
                "bc": "betweenness forward + backward passes", "kcore": "bucket peeling"}
 
@@ -234,6 +240,10 @@ def bytes_model(kind, n, st):
     """Algorithmic bytes of one query (every access counted once, 4 B per
     word, random or not), from the device statistics of the query."""
     E, V, R, I = st["edges_scanned"], st["vertices_expanded"], st["relaxations"], st["bucket_inserts"]
+    if kind == "delta":
+        # as wBFS, plus the expansion stamps and side-list flags set up (4n +
+        # n/4) and one stamp exchange per extracted entry (4)
+        return 8 * n + n // 4 + 24 * I + 12 * E + 8 * R + 16 * st["heavy_vertices"]
     if kind == "wbfs":
         # init D (4n); per filing: the bucket write, then at extraction the
         # ring slot, D[v], offsets pair (20; filings I, stale ones included,
@@ -243,12 +253,13 @@ def bytes_model(kind, n, st):
         return 4 * n + 20 * I + 12 * E + 8 * R + 16 * st["heavy_vertices"]
     if kind == "kcore":
         # init remaining degrees and the finished bitmap (4n + n/8); per
-        # bucket k two passes over them (remaining degree and finished word
-        # of every vertex); per arc of a peeled vertex: target, its remaining
-        # degree, the fetch-and-add (12); per vertex: queue entry written and
-        # read, coreness written (16)
-        nk = st.get("buckets", 1)
-        return 4 * n + n // 8 + nk * 2 * (4 * n + n // 8) + 12 * E + 16 * n
+        # bucket one pass over them (remaining degree and finished word of
+        # every vertex; the next bucket's minimum is gathered in the same
+        # pass); per arc of a peeled vertex: target, its remaining degree, the
+        # fetch-and-add (12); per vertex: queue entry written and read,
+        # coreness written (16)
+        nk = st["rounds"] - st["push_rounds"]  # bucket passes (rounds counts both kinds)
+        return 4 * n + n // 8 + nk * (4 * n + n // 8) + 12 * E + 16 * n
     if kind == "bc":
         # init path counts, dependencies (fp64) and levels (20n); per scanned
         # arc in either pass: target, its level, one 8-byte value (16); per
@@ -298,7 +309,7 @@ def cpu_reference_sample(g, wl, srcs, budget_s=15.0, max_queries=None):
     done = 0
     for s in srcs:
         t0 = time.perf_counter()
-        if wl["kind"] == "wbfs":
+        if wl["kind"] in ("wbfs", "delta"):
             d = oracle.dijkstra(g, int(s))
         elif wl["kind"] == "bf":
             d = oracle.bellman_ford(g, int(s))
@@ -657,6 +668,8 @@ def main():
     def launch(i):
         if kind == "wbfs":
             gb.gbf_wbfs(graph.h, int(srcs[i]), outs[i], opt, stream)
+        elif kind == "delta":
+            gb.gbf_delta_stepping(graph.h, int(srcs[i]), wl["delta"], outs[i], opt, stream)
         elif kind == "bf":
             gb.gbf_bellman_ford(graph.h, int(srcs[i]), outs[i], opt, stream)
         elif kind == "widest":
@@ -677,7 +690,6 @@ def main():
                 stats.append(gb.gbf_wait(graph.h, stream))
                 if kind == "kcore":
                     te.append(g.m // 2)
-                    stats[-1]["buckets"] = int(np.unique(outs[i].cpu().numpy()).size)
                 elif kind == "bc":
                     # the component, from one untimed BFS of this library
                     hops = torch.empty(n, dtype=torch.int32, device=dev)
@@ -741,6 +753,8 @@ def main():
         for i in range(len(srcs)):
             if kind == "wbfs":
                 gb.gbf_wbfs(graph.h, int(srcs[i]), host_out[i], opt, None)
+            elif kind == "delta":
+                gb.gbf_delta_stepping(graph.h, int(srcs[i]), wl["delta"], host_out[i], opt, None)
             elif kind == "bf":
                 gb.gbf_bellman_ford(graph.h, int(srcs[i]), host_out[i], opt, None)
             elif kind == "widest":
@@ -759,7 +773,8 @@ def main():
     e2e_val = te_all * e2e_steps / e2e_s / 1e9
     d2h = len(srcs) * n * (8 if kind == "bc" else 4 * (2 if kind == "bfs" else 1))
 
-    kname = "bf_kernel" if kind == "widest" else f"{kind}_kernel"  # widest runs the BF kernel
+    # widest path runs the Bellman-Ford kernel, Δ-stepping the wBFS kernel
+    kname = {"widest": "bf_kernel", "delta": "wbfs_kernel"}.get(kind, f"{kind}_kernel")
     line = None
     if rank == 0:
         cpu = None
