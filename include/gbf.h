@@ -81,7 +81,9 @@ typedef struct gbf_graph gbf_graph;
  *   dense_wbfs    1 = let wBFS switch to a dense edgeMap for dense buckets (default 0)
  *   spin_cap_us   time limit of every bounded device wait, microseconds (default 5,000,000)
  *   counters      reserved (statistics are always collected)
- *   ctas          CTAs of the persistent kernels (default: every CTA that fits, all SMs)
+ *   ctas          CTAs of the persistent kernels (default: every CTA that fits, all SMs;
+ *                 on graphs with fewer than 8 arcs per vertex, whose many thin rounds
+ *                 cost mostly their grid barrier, half as many CTAs as SMs)
  *   pull_serial   arcs each vertex checks on its own (4 at a time) before the dense step
  *                 may walk its remaining arcs with the whole warp (0 = per kind:
  *                 128 for BFS, 8 for multi-source BFS)

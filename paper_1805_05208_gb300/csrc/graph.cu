@@ -41,7 +41,6 @@ gbf_status check_smem(size_t bytes, const char *kernel) {
 
 // ------------------------------------------------------------------ options
 Opts resolve(const gbf_options *o, const Graph &g, int kind) {
-  (void)g;
   gbf_options d;
   gbf_options_default(&d);
   if (!o) o = &d;
@@ -60,7 +59,12 @@ Opts resolve(const gbf_options *o, const Graph &g, int kind) {
   r.heavy_cutoff = std::max(hc, r.block);  // staging buffer must hold one CTA pass
   r.bucket_window = o->bucket_window;
   r.dense_wbfs = o->dense_wbfs ? 1 : 0;
-  r.ctas = o->ctas > 0 ? o->ctas : 0;
+  // ctas 0: every CTA that fits, except on sparse graphs (fewer than 8 arcs
+  // per vertex: high diameter, thin frontiers, thousands of rounds whose cost
+  // is the grid barrier), where half the SMs' worth of CTAs is faster; the
+  // 64-lane MS-BFS keeps the full grid
+  const bool sparse = g.n > 0 && (uint64_t)g.m < 8ull * (uint64_t)g.n;
+  r.ctas = o->ctas > 0 ? o->ctas : (sparse && kind != GBF_TUNE_MSBFS ? std::max(g.num_sms / 2, 1) : 0);
   // pull_serial 0: per-kind default (the BFS pull hands long scans to a warp
   // walk only rarely; the multi-source pull after a few arcs)
   r.pull_serial = o->pull_serial > 0 ? std::min(o->pull_serial, 1 << 20)
