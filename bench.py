@@ -334,6 +334,59 @@ def cpu_reference_sample(g, wl, srcs, budget_s=15.0, max_queries=None):
     return te, t, done
 
 
+def cpu_parallel_sample(tasks, budget_s, threads=None):
+    """Run independent oracle queries (callables returning a count) on all
+    host cores until about `budget_s` seconds have passed: one thread per core
+    (the oracle's C entry points release the GIL).  Returns (sum of counts,
+    queries done, wall seconds, threads)."""
+    import concurrent.futures as cf
+    threads = threads or os.cpu_count() or 1
+    it = iter(tasks)
+    total, done = 0, 0
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        futs = set()
+        for _ in range(threads):
+            nxt = next(it, None)
+            if nxt is None:
+                break
+            futs.add(ex.submit(nxt))
+        while futs:
+            fin, futs = cf.wait(futs, return_when=cf.FIRST_COMPLETED)
+            for f in fin:
+                total += f.result()
+                done += 1
+                if time.perf_counter() - t0 < budget_s:
+                    nxt = next(it, None)
+                    if nxt is not None:
+                        futs.add(ex.submit(nxt))
+    return total, done, time.perf_counter() - t0, threads
+
+
+def serve_cpu_tasks(csrs, seed):
+    """The serving mix (uniform graph, 80 % BFS / 20 % Dijkstra, sources of
+    degree > 0) as oracle calls returning 1.  At most two Dijkstra queries run
+    at once: the oracle's heap holds one entry per arc."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    heavy = threading.Semaphore(2)
+
+    def bfs(g, s):
+        return lambda: (oracle.bfs(g, s, parents=False), 1)[1]
+
+    def sssp(g, s):
+        def run():
+            with heavy:
+                oracle.dijkstra(g, s)
+            return 1
+        return run
+
+    while True:
+        j = int(rng.integers(len(csrs)))
+        s = int(G.sources(csrs[j], 1, seed=int(rng.integers(1 << 30)))[0])
+        yield sssp(csrs[j], s) if rng.random() >= 0.8 else bfs(csrs[j], s)
+
+
 def run_reference(args, wl, rank, world):
     if rank != 0:
         return 0
@@ -468,6 +521,16 @@ def run_serve(args, wl, rank, world):
     best = max(x["qps"] for x in res["batched"])
     base = max(x["qps"] for x in res["one_per_launch_fifo"])
     clocks = clk.summary()
+    cpu = cpu_all = None
+    if not args.no_cpu_baseline:
+        _, q1, t1, _ = cpu_parallel_sample(serve_cpu_tasks(csrs, seed=5), args.cpu_budget, threads=1)
+        cpu = {"value": q1 / t1, "unit": "queries/s", "cores": 1, "kind": "oracle",
+               "sample": f"{q1} queries of the serving mix (FIFO BFS / binary-heap Dijkstra), "
+                         f"{t1:.1f} s"}
+        _, qa, ta, th = cpu_parallel_sample(serve_cpu_tasks(csrs, seed=6), args.cpu_budget)
+        cpu_all = {"value": qa / ta, "unit": "queries/s", "cores": th, "kind": "oracle",
+                   "sample": f"{qa} independent queries of the serving mix, one thread per "
+                             f"host core, {ta:.1f} s"}
     line = {
         "metric": "served queries/s", "value": best, "unit": "queries/s", "n_gpus": 1,
         "steps": len(rates), "warmup": warm, "ms_per_step": None, "higher_is_better": True,
@@ -478,6 +541,8 @@ def run_serve(args, wl, rank, world):
                    "arrival_seed": 4},
         "serve": res,
         "speedup_vs_one_per_launch": best / base,
+        "cpu_baseline": cpu,
+        "cpu_baseline_all_cores": cpu_all,
         "e2e": {"value": best, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
                 "note": "submit-to-completion through the C ABI; results left on the device"},
         "gpu_launches": None,
@@ -571,6 +636,16 @@ def run_msbfs(args, wl, g, srcs, graph, opt, stream, dev, rank, world, barrier, 
             cpu = {"value": te_c / t_c / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
                    "sample": f"{q} of the {k} single-source oracle BFS runs of one step, "
                              f"{t_c:.1f} s"}
+        cpu_all = None
+        if not args.no_cpu_baseline and world == 1:
+            import oracle
+
+            def task(s_):
+                return lambda: traversed_edges(g, oracle.bfs(g, int(s_), parents=False)[0])
+            te_a, qa, ta, th = cpu_parallel_sample((task(s_) for s_ in srcs), args.cpu_budget)
+            cpu_all = {"value": te_a / ta / 1e9, "unit": "GTEPS", "cores": th, "kind": "oracle",
+                       "sample": f"{qa} of the {k} sources as independent oracle BFS runs, one "
+                                 f"thread per host core, {ta:.1f} s"}
         clocks = clk.summary()
         line = {
             "metric": "GTEPS", "value": value, "unit": "GTEPS", "n_gpus": world,
@@ -591,6 +666,7 @@ def run_msbfs(args, wl, g, srcs, graph, opt, stream, dev, rank, world, barrier, 
                          "avg_launch_ms": avg,
                          "traffic": measured_traffic(args.workload, "msbfs_kernel")},
             "cpu_baseline": cpu,
+            "cpu_baseline_all_cores": cpu_all,
             "e2e": {"value": te_all * e2e_steps / e2e_s / 1e9, "unit": "GTEPS",
                     "h2d_bytes_per_step": 4 * k, "d2h_bytes_per_step": 4 * k * n},
             "gpu_launches": args.steps,

@@ -53,3 +53,25 @@ def test_measured_traffic_needs_matching_sources(tmp_path, monkeypatch):
     assert bench.measured_traffic("w", "bfs_kernel") is None      # other kernel
     assert bench.measured_traffic("b", "bfs_kernel") is None      # sources changed since
     assert bench.measured_traffic("missing", "bfs_kernel") is None
+
+
+def test_cpu_parallel_sample_counts_every_query():
+    done = []
+
+    def task(i):
+        def run():
+            done.append(i)
+            return i
+        return run
+    total, q, wall, th = bench.cpu_parallel_sample((task(i) for i in range(10)), budget_s=60, threads=3)
+    assert q == 10 and total == sum(range(10)) and sorted(done) == list(range(10)) and th == 3
+    # a spent budget stops new submissions after the first wave
+    total, q, wall, th = bench.cpu_parallel_sample((task(i) for i in range(10)), budget_s=0, threads=3)
+    assert q == 3
+
+
+def test_serve_cpu_tasks_run_the_oracle():
+    import graphgen as G
+    csrs = [G.add_weights(G.rmat(8, 8, seed=s), 1, 22, seed=2) for s in (1, 2)]
+    _, q, _, _ = bench.cpu_parallel_sample(bench.serve_cpu_tasks(csrs, seed=5), budget_s=0.2, threads=2)
+    assert q >= 2
