@@ -27,6 +27,19 @@ def test_bytes_model_terms():
     n = 64
     assert bench.bytes_model("wbfs", n, st) == 4 * n + 20 * 5 + 12 * 10 + 8 * 4 + 16 * 2
     assert bench.bytes_model("bfs", n, st) == 8 * n + n // 8 + 12 * 3 + 8 * 10 + 24 * 6 + 3 * (n // 8)
+    assert bench.bytes_model("delta", n, st) == 8 * n + n // 4 + 24 * 5 + 12 * 10 + 8 * 4 + 16 * 2
+    # k-core: one vertex pass per bucket; rounds count bucket passes and peeling rounds
+    kst = dict(st, rounds=9, push_rounds=6)
+    assert bench.bytes_model("kcore", n, kst) == 4 * n + n // 8 + 3 * (4 * n + n // 8) + 12 * 10 + 16 * n
+
+
+def test_trace_summary_groups_rounds_by_kind():
+    tr = [(1, 5, 10, 20, 1000, 0), (2, 1, 10, 20, 4000, 0), (3, 1, 2, 3, 5000, 0),
+          (4, 5, 7, 9, 9000, 0)]
+    out = bench.trace_summary(tr)
+    assert out["rounds"] == 4 and out["end_us"] == 9.0
+    assert out["by_kind"]["bucket"] == {"rounds": 2, "us": 5.0, "frontier": 17}
+    assert out["by_kind"]["sparse"] == {"rounds": 2, "us": 4.0, "frontier": 12}
 
 
 def test_kernel_source_hash_tracks_only_its_sources():
