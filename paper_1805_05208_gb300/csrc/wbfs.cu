@@ -638,8 +638,9 @@ __global__ void __launch_bounds__(1024) wbfs_kernel(WbfsParams P) {
     } else if (hcnt > 0) {
       // heavy vertices of the bucket: blocked edgeMap over all CTAs
       QueueIn in{P.q, P.qoff, nullptr, P.cs, hcnt, hD};
-      // every heavy vertex has more than P.heavy edges
-      blocked_edge_map(g, in, chunk_shift(hD, 4u, 7),
+      // every heavy vertex has more than P.heavy edges; chunks of at most
+      // 256 << 6 arcs keep the last chunks of the round short
+      blocked_edge_map(g, in, chunk_shift(hD, 4u, 6),
                        (uint32_t)P.bmax, S, fn, fsink, ctl, bem++);
       fsink.flush(S);
       if (blockIdx.x == 0 && threadIdx.x == 0) c.scanned += hD;
