@@ -7,8 +7,11 @@
  *   - BFS (§4 problem statement; Alg. 1),
  *   - integral-weight SSSP / weighted BFS over Julienne buckets (§4; Alg. 3),
  * plus a 64-lane bit-packed multi-source BFS and a continuous-batching query
- * server.  All arithmetic is integer: int32 distances and ids, uint32 offsets
- * and weights.
+ * server, and further problems on the same edgeMap and bucket structure:
+ * Bellman-Ford and widest path (Alg. 4), single-source betweenness (Alg. 2),
+ * k-core (Alg. 16) and Δ-stepping.  All arithmetic is integer (int32
+ * distances and ids, uint32 offsets and weights) except betweenness, whose
+ * path counts and dependencies are fp64.
  *
  * Conventions for every call:
  *   - Every function returns a gbf_status, never aborts, never throws across

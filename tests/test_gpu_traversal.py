@@ -268,3 +268,27 @@ def test_round_trace(gb):
     g.wbfs(s)
     tr = gb.gbf_trace(g.h)
     assert len(tr) == g.stats()["rounds"] > 0
+
+
+def test_sparse_graphs_default_to_half_the_sms(gb):
+    """With ctas left at 0, a graph with fewer than 8 arcs per vertex runs on
+    half as many CTAs as SMs; a denser graph gets every resident CTA.  The
+    distances do not depend on it."""
+    torch = pytest.importorskip("torch")
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    sparse = G.add_weights(G.grid(60, 70, 0.1, seed=3), 1, 16, seed=4)
+    dense = G.add_weights(G.rmat(12, 16, seed=5), 1, 22, seed=6)
+    for csr, expect_half in ((sparse, True), (dense, False)):
+        g = gb.Graph(csr)
+        s = int(G.sources(csr, 1, seed=7)[0])
+        d = torch.empty(csr.n, dtype=torch.int32, device="cuda")
+        for run in (lambda: gb.gbf_bfs(g.h, s, d), lambda: gb.gbf_wbfs(g.h, s, d),
+                    lambda: gb.gbf_delta_stepping(g.h, s, 4, d)):
+            run()
+            st = gb.gbf_wait(g.h)
+            if expect_half:
+                assert st["grid_ctas"] == max(sms // 2, 1), csr.name
+            else:
+                assert st["grid_ctas"] > sms // 2, csr.name
+        assert np.array_equal(d.cpu().numpy(), oracle.dijkstra(csr, s))
+        g.close()
