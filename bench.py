@@ -334,6 +334,31 @@ def cpu_reference_sample(g, wl, srcs, budget_s=15.0, max_queries=None):
     return te, t, done
 
 
+_ARM_PARTS = {0xd0c: "Neoverse-N1", 0xd40: "Neoverse-V1", 0xd49: "Neoverse-N2",
+              0xd4f: "Neoverse-V2", 0xd8e: "Neoverse-N3", 0xd84: "Neoverse-V3"}
+
+
+def host_cpu():
+    """The host CPU the oracle is timed on: model and logical cores."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                k, v = k.strip(), v.strip()
+                if k == "model name" and v:
+                    model = v
+                    break
+                if k == "CPU part" and v:
+                    part = int(v, 16)
+                    model = _ARM_PARTS.get(part, f"Arm part {v}")
+                    break
+    except (OSError, ValueError):
+        pass
+    import platform
+    return {"model": model or platform.machine(), "nproc": os.cpu_count()}
+
+
 def cpu_parallel_sample(tasks, budget_s, threads=None):
     """Run independent oracle queries (callables returning a count) on all
     host cores until about `budget_s` seconds have passed: one thread per core
@@ -408,6 +433,7 @@ def run_reference(args, wl, rank, world):
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": args.workload, "desc": wl["desc"]},
             "cpu_baseline": {"value": gteps, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                             "host": host_cpu(),
                              "sample": f"{q} single-source oracle queries (one per step) of the "
                                        f"{wl['nsrc']}-source step, 1 thread"},
             "e2e": {"value": gteps, "unit": "GTEPS", "h2d_bytes_per_step": 0,
@@ -524,11 +550,12 @@ def run_serve(args, wl, rank, world):
     cpu = cpu_all = None
     if not args.no_cpu_baseline:
         _, q1, t1, _ = cpu_parallel_sample(serve_cpu_tasks(csrs, seed=5), args.cpu_budget, threads=1)
-        cpu = {"value": q1 / t1, "unit": "queries/s", "cores": 1, "kind": "oracle",
+        cpu = {"value": q1 / t1, "unit": "queries/s", "cores": 1, "kind": "oracle", "host": host_cpu(),
                "sample": f"{q1} queries of the serving mix (FIFO BFS / binary-heap Dijkstra), "
                          f"{t1:.1f} s"}
         _, qa, ta, th = cpu_parallel_sample(serve_cpu_tasks(csrs, seed=6), args.cpu_budget)
         cpu_all = {"value": qa / ta, "unit": "queries/s", "cores": th, "kind": "oracle",
+                   "host": host_cpu(),
                    "sample": f"{qa} independent queries of the serving mix, one thread per "
                              f"host core, {ta:.1f} s"}
     line = {
@@ -634,6 +661,7 @@ def run_msbfs(args, wl, g, srcs, graph, opt, stream, dev, rank, world, barrier, 
             te_c, t_c, q = cpu_reference_sample(g, dict(wl, kind="bfs"), srcs,
                                                 budget_s=args.cpu_budget)
             cpu = {"value": te_c / t_c / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                   "host": host_cpu(),
                    "sample": f"{q} of the {k} single-source oracle BFS runs of one step, "
                              f"{t_c:.1f} s"}
         cpu_all = None
@@ -644,6 +672,7 @@ def run_msbfs(args, wl, g, srcs, graph, opt, stream, dev, rank, world, barrier, 
                 return lambda: traversed_edges(g, oracle.bfs(g, int(s_), parents=False)[0])
             te_a, qa, ta, th = cpu_parallel_sample((task(s_) for s_ in srcs), args.cpu_budget)
             cpu_all = {"value": te_a / ta / 1e9, "unit": "GTEPS", "cores": th, "kind": "oracle",
+                       "host": host_cpu(),
                        "sample": f"{qa} of the {k} sources as independent oracle BFS runs, one "
                                  f"thread per host core, {ta:.1f} s"}
         clocks = clk.summary()
@@ -857,6 +886,7 @@ def main():
         if not args.no_cpu_baseline and world == 1:
             te_c, t_c, q = cpu_reference_sample(g, wl, srcs, budget_s=args.cpu_budget)
             cpu = {"value": te_c / t_c / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                   "host": host_cpu(),
                    "sample": f"{q} of the {len(srcs)} queries of one step, serial oracle "
                              f"({ORACLE_NAME[kind]}), "
                              f"{t_c:.1f} s"}

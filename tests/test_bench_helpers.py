@@ -88,3 +88,8 @@ def test_serve_cpu_tasks_run_the_oracle():
     csrs = [G.add_weights(G.rmat(8, 8, seed=s), 1, 22, seed=2) for s in (1, 2)]
     _, q, _, _ = bench.cpu_parallel_sample(bench.serve_cpu_tasks(csrs, seed=5), budget_s=0.2, threads=2)
     assert q >= 2
+
+
+def test_host_cpu_names_model_and_cores():
+    h = bench.host_cpu()
+    assert h["nproc"] == os.cpu_count() and isinstance(h["model"], str) and h["model"]
