@@ -67,6 +67,8 @@ def _load():
             lib.or_betweenness.restype = ctypes.c_int64
             lib.or_coreness.argtypes = [ctypes.c_int32, P, P, P]
             lib.or_coreness.restype = ctypes.c_int64
+            lib.or_components.argtypes = [ctypes.c_int32, P, P, P]
+            lib.or_components.restype = ctypes.c_int64
             lib.or_floyd_warshall.argtypes = [ctypes.c_int32, P, P, P, P]
             lib.or_floyd_warshall.restype = ctypes.c_int
             lib.or_check_bfs.argtypes = [ctypes.c_int32, P, P, ctypes.c_int32, P, P,
@@ -177,6 +179,19 @@ def coreness(g):
     if rc < 0:
         raise ValueError("or_coreness: bad argument")
     return core
+
+
+def components(g):
+    """Connected components (§4 "Connectivity"): int32 label[v] = the smallest
+    vertex id in v's component."""
+    lib = _load()
+    off, po = _c(g.off, np.uint32)
+    tgt = np.ascontiguousarray(g.tgt, dtype=np.int32) if g.m else np.zeros(1, np.int32)
+    label = np.empty(max(g.n, 1), dtype=np.int32)[:g.n]
+    rc = lib.or_components(g.n, po, tgt.ctypes.data, label.ctypes.data)
+    if rc < 0:
+        raise ValueError("or_components: bad argument")
+    return label
 
 
 def floyd_warshall(g, weighted: bool):

@@ -27,8 +27,13 @@
  *     largest k such that v lies in a subgraph whose vertices all have
  *     degree >= k.  The oracle is the textbook bucket peeling (repeatedly
  *     remove a vertex of minimum current degree; its coreness is the largest
- *     minimum seen so far), pinned against the definition by brute force.  Floyd–Warshall is included as a brute-force check for tiny
- * graphs.  Infinity is INT32_MAX; unreachable parents are -1; the parent of
+ *     minimum seen so far), pinned against the definition by brute force.
+ *   - Connectivity (§4 "Connectivity"): label[v] = the smallest vertex id in
+ *     v's connected component, a canonical form of the unique partition (the
+ *     paper's Alg. 7 reaches the partition through low-diameter
+ *     decompositions; any labelling of it maps to this one).  Computed by a
+ *     FIFO search from each vertex, in increasing id, not yet labelled.
+ * Floyd–Warshall is included as a brute-force check for tiny graphs.  Infinity is INT32_MAX; unreachable parents are -1; the parent of
  * the source is the source itself.
  *
  * The validators state the invariants that any correct BFS tree / shortest-
@@ -314,6 +319,37 @@ int64_t or_betweenness(int32_t n, const uint32_t *off, const int32_t *tgt, int32
  * give it coreness k = max(k, its degree), and lower each remaining
  * neighbour's degree by one, moving it one bucket down.  Buckets are doubly
  * linked lists.  Returns the largest coreness, or -1 on a bad argument. */
+/* Connected components: label[v] = smallest id in v's component.  Returns
+ * the number of components, or -1 on a bad argument / allocation failure. */
+int64_t or_components(int32_t n, const uint32_t *off, const int32_t *tgt, int32_t *label) {
+  if (n < 0) return -1;
+  if (n == 0) return 0;
+  int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+  if (!queue) return -1;
+  for (int32_t v = 0; v < n; v++) label[v] = -1;
+  int64_t comps = 0;
+  for (int32_t s = 0; s < n; s++) {
+    if (label[s] >= 0) continue;
+    /* every smaller id is labelled already, so s is its component's minimum */
+    comps++;
+    label[s] = s;
+    int64_t head = 0, tail = 0;
+    queue[tail++] = s;
+    while (head < tail) {
+      const int32_t u = queue[head++];
+      for (uint32_t e = off[u]; e < off[u + 1]; e++) {
+        const int32_t v = tgt[e];
+        if (label[v] < 0) {
+          label[v] = s;
+          queue[tail++] = v;
+        }
+      }
+    }
+  }
+  free(queue);
+  return comps;
+}
+
 int64_t or_coreness(int32_t n, const uint32_t *off, const int32_t *tgt, int32_t *core) {
   if (n <= 0) return -1;
   int32_t maxd = 0;
