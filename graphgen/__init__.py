@@ -167,6 +167,13 @@ def sources(g: CSR, k: int, seed: int = 3) -> np.ndarray:
     return out
 
 
+def exp_shifts(n: int, beta: float, seed: int = 5) -> np.ndarray:
+    """n seeded draws from the exponential distribution with rate beta
+    (float64): the random shifts a low-diameter decomposition draws, passed
+    to it as an input."""
+    return np.random.default_rng(_u64(seed, n) & 0xffffffff).exponential(1.0 / beta, size=n)
+
+
 def max_degree_vertex(g: CSR) -> int:
     """Highest-degree vertex, ties broken by the lowest id."""
     return int(_load().gg_max_degree_vertex(g.n, g.off.ctypes.data))

@@ -44,7 +44,7 @@ def build(force: bool = False) -> str:
         return _SO
     os.makedirs(os.path.dirname(_SO), exist_ok=True)
     tmp = _SO + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, src])
+    subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, src, "-lm"])
     os.replace(tmp, _SO)
     return _SO
 
@@ -69,6 +69,8 @@ def _load():
             lib.or_coreness.restype = ctypes.c_int64
             lib.or_components.argtypes = [ctypes.c_int32, P, P, P]
             lib.or_components.restype = ctypes.c_int64
+            lib.or_ldd.argtypes = [ctypes.c_int32, P, P, P, P, P]
+            lib.or_ldd.restype = ctypes.c_int64
             lib.or_floyd_warshall.argtypes = [ctypes.c_int32, P, P, P, P]
             lib.or_floyd_warshall.restype = ctypes.c_int
             lib.or_check_bfs.argtypes = [ctypes.c_int32, P, P, ctypes.c_int32, P, P,
@@ -192,6 +194,24 @@ def components(g):
     if rc < 0:
         raise ValueError("or_components: bad argument")
     return label
+
+
+def ldd(g, delta):
+    """Low-diameter decomposition (§4; Alg. 6) with the given shifts
+    delta[v] ~ Exp(beta): (C, T), C[v] the centre of v's cluster (one valid
+    choice where searches tie), T[v] the round v joined a frontier."""
+    lib = _load()
+    off, po = _c(g.off, np.uint32)
+    tgt = np.ascontiguousarray(g.tgt, dtype=np.int32) if g.m else np.zeros(1, np.int32)
+    d = np.ascontiguousarray(delta, dtype=np.float64)
+    if d.shape != (g.n,):
+        raise ValueError("delta must have one entry per vertex")
+    C = np.empty(max(g.n, 1), dtype=np.int32)[:g.n]
+    T = np.empty(max(g.n, 1), dtype=np.int32)[:g.n]
+    rc = lib.or_ldd(g.n, po, tgt.ctypes.data, d.ctypes.data, C.ctypes.data, T.ctypes.data)
+    if rc < 0:
+        raise ValueError("or_ldd: bad argument")
+    return C, T
 
 
 def floyd_warshall(g, weighted: bool):

@@ -33,6 +33,14 @@
  *     paper's Alg. 7 reaches the partition through low-diameter
  *     decompositions; any labelling of it maps to this one).  Computed by a
  *     FIFO search from each vertex, in increasing id, not yet labelled.
+ *   - Low-diameter decomposition (§4; Alg. 6, Miller–Peng–Xu): given the
+ *     shifts delta[v] ~ Exp(beta) as an input, vertex v may start its own
+ *     cluster in round floor(max delta - delta[v]) if nothing has reached it;
+ *     each round every frontier vertex hands its cluster to its unclaimed
+ *     neighbours.  The round T[v] in which v joins a frontier is unique;
+ *     which cluster wins a tie is not, so C is one valid assignment (the
+ *     first claimant in frontier order) and tests check T exactly and C by
+ *     its invariants.
  * Floyd–Warshall is included as a brute-force check for tiny graphs.  Infinity is INT32_MAX; unreachable parents are -1; the parent of
  * the source is the source itself.
  *
@@ -43,6 +51,7 @@
  * Inputs: symmetric CSR, uint32 offsets off[0..n], int32 targets tgt[0..m),
  * optional uint32 weights w[0..m).
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -348,6 +357,78 @@ int64_t or_components(int32_t n, const uint32_t *off, const int32_t *tgt, int32_
   }
   free(queue);
   return comps;
+}
+
+/* Low-diameter decomposition rounds (Alg. 6).  C[v] = centre of v's cluster,
+ * T[v] = round in which v joined a frontier.  Returns the number of
+ * clusters, or -1 on a bad argument / allocation failure. */
+int64_t or_ldd(int32_t n, const uint32_t *off, const int32_t *tgt, const double *delta,
+               int32_t *C, int32_t *T) {
+  if (n < 0) return -1;
+  if (n == 0) return 0;
+  double dmax = delta[0];
+  for (int32_t v = 1; v < n; v++)
+    if (delta[v] > dmax) dmax = delta[v];
+  /* start round of v: the first round r with Start[v] = dmax - delta[v] < r + 1 */
+  int64_t *start = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+  int32_t *order = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+  int32_t *F = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+  int32_t *F2 = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+  int64_t maxs = 0;
+  if (!start || !order || !F || !F2) {
+    free(start); free(order); free(F); free(F2);
+    return -1;
+  }
+  for (int32_t v = 0; v < n; v++) {
+    const double s = floor(dmax - delta[v]);
+    start[v] = s < 0 ? 0 : (int64_t)s;
+    if (start[v] > maxs) maxs = start[v];
+  }
+  /* vertices by start round (counting sort; ties by id) */
+  int64_t *cnt = (int64_t *)calloc((size_t)maxs + 2, sizeof(int64_t));
+  if (!cnt) {
+    free(start); free(order); free(F); free(F2);
+    return -1;
+  }
+  for (int32_t v = 0; v < n; v++) cnt[start[v] + 1]++;
+  for (int64_t r = 0; r <= maxs; r++) cnt[r + 1] += cnt[r];
+  for (int32_t v = 0; v < n; v++) order[cnt[start[v]]++] = v;
+  free(cnt);
+  for (int32_t v = 0; v < n; v++) C[v] = T[v] = -1;
+  int64_t visited = 0, clusters = 0, fs = 0, next = 0;
+  for (int64_t r = 0; visited < n; r++) {
+    /* vertices whose start round has come and that nothing has reached */
+    while (next < n && start[order[next]] <= r) {
+      const int32_t v = order[next++];
+      if (C[v] < 0) {
+        C[v] = v;
+        T[v] = (int32_t)r;
+        F[fs++] = v;
+        visited++;
+        clusters++;
+      }
+    }
+    /* edgeMap: the frontier hands its clusters to unclaimed neighbours */
+    int64_t fs2 = 0;
+    for (int64_t i = 0; i < fs; i++) {
+      const int32_t u = F[i];
+      for (uint32_t e = off[u]; e < off[u + 1]; e++) {
+        const int32_t d = tgt[e];
+        if (C[d] < 0) {
+          C[d] = C[u];
+          T[d] = (int32_t)(r + 1);
+          F2[fs2++] = d;
+          visited++;
+        }
+      }
+    }
+    int32_t *tmp = F;
+    F = F2;
+    F2 = tmp;
+    fs = fs2;
+  }
+  free(start); free(order); free(F); free(F2);
+  return clusters;
 }
 
 int64_t or_coreness(int32_t n, const uint32_t *off, const int32_t *tgt, int32_t *core) {
