@@ -264,9 +264,30 @@ gbf_status gbf_kcore(gbf_graph *g, int32_t *core, int mem, const gbf_options *op
                      void *cuda_stream);
 
 /*
+ * gbf_ldd — low-diameter decomposition (§4 "Low-Diameter Decomposition";
+ * Alg. 6, the Miller-Peng-Xu clustering): vertex v may start its own cluster
+ * in round floor(max delta - delta[v]) unless a search has reached it; every
+ * round each frontier vertex hands its cluster to its unclaimed neighbours
+ * (compare-and-swap), which form the next frontier.
+ *   delta    fp64[n]: the shifts, drawn by the caller from Exp(beta); finite,
+ *            >= 0, with max delta - min delta < 2^22
+ *   cluster  int32[n]: the centre of v's cluster (a centre is its own)
+ *   round    int32[n]: the round in which v joined a frontier (unique; which
+ *            of several searches reaching v in one round wins is not)
+ *   mem      GBF_HOST: all three are host buffers, blocks; GBF_DEVICE: all
+ *            three are device pointers, stream-ordered, see gbf_wait
+ * Errors: GBF_ERR_INVALID for NULL arguments or negative / non-finite /
+ * too widely spread shifts (reported by the device; outputs undefined);
+ * GBF_ERR_TIMEOUT as gbf_bfs.
+ */
+gbf_status gbf_ldd(gbf_graph *g, const double *delta, int32_t *cluster, int32_t *round, int mem,
+                   const gbf_options *opt, void *cuda_stream);
+
+/*
  * gbf_wait — synchronise `cuda_stream` and return the device-side status of
  * the last gbf_bfs / gbf_wbfs / gbf_msbfs / gbf_bellman_ford /
- * gbf_widest_path / gbf_betweenness / gbf_kcore issued on g with GBF_DEVICE
+ * gbf_widest_path / gbf_betweenness / gbf_kcore / gbf_delta_stepping /
+ * gbf_ldd issued on g with GBF_DEVICE
  * buffers; fills *stats if non-NULL.
  */
 gbf_status gbf_wait(gbf_graph *g, void *cuda_stream, gbf_stats *stats);

@@ -101,6 +101,7 @@ def _load() -> ctypes.CDLL:
         "gbf_bfs": (S, [P, I32, P, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
         "gbf_wbfs": (S, [P, I32, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
         "gbf_delta_stepping": (S, [P, I32, I32, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
+        "gbf_ldd": (S, [P, P, P, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
         "gbf_bellman_ford": (S, [P, I32, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
         "gbf_widest_path": (S, [P, I32, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
         "gbf_betweenness": (S, [P, I32, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
@@ -233,6 +234,18 @@ def gbf_delta_stepping(h: int, src: int, delta: int, dist, opt: Optional[gbf_opt
     pd, mem = _ptr(dist)
     _check(_lib.gbf_delta_stepping(h, int(src), int(delta), pd, mem, _opt(opt), _stream(stream)),
            "gbf_delta_stepping")
+
+
+def gbf_ldd(h: int, delta, cluster, rnd, opt: Optional[gbf_options] = None, stream=None) -> None:
+    """Low-diameter decomposition with the given shifts (float64, one per
+    vertex) into cluster (centres) and rnd (join rounds); all three in the
+    same memory."""
+    pd, md = _ptr(delta)
+    pc, mc = _ptr(cluster)
+    pr, mr = _ptr(rnd)
+    if not (md == mc == mr):
+        raise ValueError("delta, cluster and rnd must live in the same memory")
+    _check(_lib.gbf_ldd(h, pd, pc, pr, mc, _opt(opt), _stream(stream)), "gbf_ldd")
 
 
 def gbf_bellman_ford(h: int, src: int, dist, opt: Optional[gbf_options] = None,
@@ -424,6 +437,13 @@ class Graph:
         d = np.empty(self.n, dtype=np.int32)
         gbf_delta_stepping(self.h, src, delta, d, opt)
         return d
+
+    def ldd(self, delta, opt=None):
+        d = np.ascontiguousarray(delta, dtype=np.float64)
+        c = np.empty(self.n, dtype=np.int32)
+        t = np.empty(self.n, dtype=np.int32)
+        gbf_ldd(self.h, d, c, t, opt)
+        return c, t
 
     def bellman_ford(self, src: int, opt=None):
         d = np.empty(self.n, dtype=np.int32)
