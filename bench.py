@@ -59,6 +59,10 @@ WORKLOADS = {
     "kcore-rmat22": dict(kind="kcore", graph="rmat", scale=22, ef=16, w=None, nsrc=1,
                          desc="coreness of every vertex (Alg. 16 peeling), RMAT scale 22 ef16; "
                               "one step = one full decomposition; GTEPS = undirected edges / time"),
+    "ldd-rmat22": dict(kind="ldd", beta=0.2, graph="rmat", scale=22, ef=16, w=None, nsrc=1,
+                       desc="low-diameter decomposition (Alg. 6), beta 0.2, shifts seeded "
+                            "(graphgen.exp_shifts, seed 5), RMAT scale 22 ef16; one step = one "
+                            "decomposition; GTEPS = undirected edges / time"),
     "wbfs-rmat26": dict(kind="wbfs", graph="rmat", scale=26, ef=16, w=(1, 22), nsrc=2,
                         desc="wBFS, RMAT scale 26 ef16, w in [1,22), 2 seeded sources"),
     "msbfs-rmat24": dict(kind="msbfs", graph="rmat", scale=24, ef=16, w=None, nsrc=64,
@@ -124,6 +128,7 @@ def make_sources(g, wl, rank=0):
 
 
 ORACLE_NAME = {"bfs": "FIFO BFS", "wbfs": "binary-heap Dijkstra", "delta": "binary-heap Dijkstra",
+               "ldd": "MPX rounds",
                "bf": "frontier Bellman-Ford", "widest": "(max,min) Bellman-Ford rounds",
                "bc": "betweenness forward + backward passes", "kcore": "bucket peeling"}
 
@@ -207,6 +212,7 @@ KERNEL_SOURCES = {
     "bf_kernel": ("bellman_ford.cu", "dev_common.cuh", "gbf_impl.h"),
     "bc_kernel": ("betweenness.cu", "dev_common.cuh", "gbf_impl.h"),
     "kcore_kernel": ("kcore.cu", "dev_common.cuh", "gbf_impl.h"),
+    "ldd_kernel": ("ldd.cu", "dev_common.cuh", "gbf_impl.h"),
 }
 
 
@@ -251,6 +257,12 @@ def bytes_model(kind, n, st):
         # per successful writeMin: atomicMin and the degree-1 bitmap word (8);
         # per heavy vertex: queue + degree prefix written and read (16)
         return 4 * n + 20 * I + 12 * E + 8 * R + 16 * st["heavy_vertices"]
+    if kind == "ldd":
+        # read the shifts (8n), write C and T (8n); per round the centre pass
+        # reads C and T of every vertex (8n); per frontier vertex its queue
+        # entry, prefix and first arc written and read (24); per scanned arc:
+        # target, the source's cluster, the target's cluster (12)
+        return 16 * n + st["rounds"] * 8 * n + 24 * n + 12 * E
     if kind == "kcore":
         # init remaining degrees and the finished bitmap (4n + n/8); per
         # bucket one pass over them (remaining degree and finished word of
@@ -324,6 +336,9 @@ def cpu_reference_sample(g, wl, srcs, budget_s=15.0, max_queries=None):
         elif wl["kind"] == "kcore":
             oracle.coreness(g)
             d = np.zeros(g.n, dtype=np.int64)  # every edge is processed
+        elif wl["kind"] == "ldd":
+            oracle.ldd(g, G.exp_shifts(g.n, wl["beta"], seed=5))
+            d = np.zeros(g.n, dtype=np.int64)
         else:
             d, _ = oracle.bfs(g, int(s))
         t += time.perf_counter() - t0
@@ -768,6 +783,10 @@ def main():
         return run_msbfs(args, wl, g, srcs, graph, opt, stream, dev, rank, world, barrier, dist_mod)
     out_dtype = torch.float64 if kind == "bc" else torch.int32
     outs = [torch.empty(n, dtype=out_dtype, device=dev) for _ in srcs]
+    if kind == "ldd":  # the shifts are an input; the join rounds a second output
+        ldd_delta = G.exp_shifts(n, wl["beta"], seed=5)
+        ldd_delta_dev = torch.from_numpy(ldd_delta).to(dev)
+        ldd_rounds = torch.empty(n, dtype=torch.int32, device=dev)
     pars = [torch.empty(n, dtype=torch.int32, device=dev) for _ in srcs] if kind == "bfs" else None
 
     def launch(i):
@@ -783,6 +802,8 @@ def main():
             gb.gbf_betweenness(graph.h, int(srcs[i]), outs[i], opt, stream)
         elif kind == "kcore":
             gb.gbf_kcore(graph.h, outs[i], opt, stream)
+        elif kind == "ldd":
+            gb.gbf_ldd(graph.h, ldd_delta_dev, outs[i], ldd_rounds, opt, stream)
         else:
             gb.gbf_bfs(graph.h, int(srcs[i]), outs[i], pars[i], opt, stream)
 
@@ -793,7 +814,7 @@ def main():
             launch(i)
             if w == 0:
                 stats.append(gb.gbf_wait(graph.h, stream))
-                if kind == "kcore":
+                if kind in ("kcore", "ldd"):
                     te.append(g.m // 2)
                 elif kind == "bc":
                     # the component, from one untimed BFS of this library
@@ -850,6 +871,7 @@ def main():
     host_out = [torch.empty(n, dtype=out_dtype, pin_memory=True).numpy() for _ in srcs]
     host_par = [torch.empty(n, dtype=torch.int32, pin_memory=True).numpy() for _ in srcs] \
         if kind == "bfs" else None
+    host_rounds = torch.empty(n, dtype=torch.int32, pin_memory=True).numpy() if kind == "ldd" else None
     e2e_steps = max(1, min(args.steps, 5))
     torch.cuda.synchronize()
     barrier()
@@ -868,6 +890,8 @@ def main():
                 gb.gbf_betweenness(graph.h, int(srcs[i]), host_out[i], opt, None)
             elif kind == "kcore":
                 gb.gbf_kcore(graph.h, host_out[i], opt, None)
+            elif kind == "ldd":
+                gb.gbf_ldd(graph.h, ldd_delta, host_out[i], host_rounds, opt, None)
             else:
                 gb.gbf_bfs(graph.h, int(srcs[i]), host_out[i], host_par[i], opt, None)
     e2e_s = time.perf_counter() - t0
@@ -876,7 +900,7 @@ def main():
         dist_mod.all_reduce(t, op=dist_mod.ReduceOp.MAX)
         e2e_s = float(t.item())
     e2e_val = te_all * e2e_steps / e2e_s / 1e9
-    d2h = len(srcs) * n * (8 if kind == "bc" else 4 * (2 if kind == "bfs" else 1))
+    d2h = len(srcs) * n * (8 if kind == "bc" else 4 * (2 if kind in ("bfs", "ldd") else 1))
 
     # widest path runs the Bellman-Ford kernel, Δ-stepping the wBFS kernel
     kname = {"widest": "bf_kernel", "delta": "wbfs_kernel"}.get(kind, f"{kind}_kernel")
@@ -907,7 +931,8 @@ def main():
                          "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_launch_ms,
                          "traffic": measured_traffic(args.workload, kname)},
             "cpu_baseline": cpu,
-            "e2e": {"value": e2e_val, "unit": "GTEPS", "h2d_bytes_per_step": 4 * len(srcs),
+            "e2e": {"value": e2e_val, "unit": "GTEPS",
+                    "h2d_bytes_per_step": 8 * n if kind == "ldd" else 4 * len(srcs),
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": args.steps * len(srcs),
             "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
