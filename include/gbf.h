@@ -284,10 +284,25 @@ gbf_status gbf_ldd(gbf_graph *g, const double *delta, int32_t *cluster, int32_t 
                    const gbf_options *opt, void *cuda_stream);
 
 /*
+ * gbf_connectivity — connected components (§4 "Connectivity"): label[v] = the
+ * smallest vertex id in v's component.  Rounds of hooking over every arc
+ * (writeMin of the smaller label into the larger label and into the vertex
+ * it names) and shortcutting (L[v] = L[L[v]]) until a round changes nothing;
+ * the paper's decomposition-contraction recursion (Alg. 7) is not used.
+ *   label   int32[n]
+ *   mem     GBF_HOST: blocks; GBF_DEVICE: stream-ordered, see gbf_wait
+ * Errors: GBF_ERR_INVALID for NULL arguments; GBF_ERR_OVERFLOW after 4,096
+ * rounds without convergence (not expected: labels halve their distance to
+ * the component's root about every round); GBF_ERR_TIMEOUT as gbf_bfs.
+ */
+gbf_status gbf_connectivity(gbf_graph *g, int32_t *label, int mem, const gbf_options *opt,
+                            void *cuda_stream);
+
+/*
  * gbf_wait — synchronise `cuda_stream` and return the device-side status of
  * the last gbf_bfs / gbf_wbfs / gbf_msbfs / gbf_bellman_ford /
  * gbf_widest_path / gbf_betweenness / gbf_kcore / gbf_delta_stepping /
- * gbf_ldd issued on g with GBF_DEVICE
+ * gbf_ldd / gbf_connectivity issued on g with GBF_DEVICE
  * buffers; fills *stats if non-NULL.
  */
 gbf_status gbf_wait(gbf_graph *g, void *cuda_stream, gbf_stats *stats);

@@ -102,6 +102,7 @@ def _load() -> ctypes.CDLL:
         "gbf_wbfs": (S, [P, I32, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
         "gbf_delta_stepping": (S, [P, I32, I32, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
         "gbf_ldd": (S, [P, P, P, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
+        "gbf_connectivity": (S, [P, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
         "gbf_bellman_ford": (S, [P, I32, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
         "gbf_widest_path": (S, [P, I32, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
         "gbf_betweenness": (S, [P, I32, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
@@ -246,6 +247,12 @@ def gbf_ldd(h: int, delta, cluster, rnd, opt: Optional[gbf_options] = None, stre
     if not (md == mc == mr):
         raise ValueError("delta, cluster and rnd must live in the same memory")
     _check(_lib.gbf_ldd(h, pd, pc, pr, mc, _opt(opt), _stream(stream)), "gbf_ldd")
+
+
+def gbf_connectivity(h: int, label, opt: Optional[gbf_options] = None, stream=None) -> None:
+    """Connected components into label (the smallest vertex id of each component)."""
+    pl, mem = _ptr(label)
+    _check(_lib.gbf_connectivity(h, pl, mem, _opt(opt), _stream(stream)), "gbf_connectivity")
 
 
 def gbf_bellman_ford(h: int, src: int, dist, opt: Optional[gbf_options] = None,
@@ -437,6 +444,11 @@ class Graph:
         d = np.empty(self.n, dtype=np.int32)
         gbf_delta_stepping(self.h, src, delta, d, opt)
         return d
+
+    def connectivity(self, opt=None):
+        lab = np.empty(self.n, dtype=np.int32)
+        gbf_connectivity(self.h, lab, opt)
+        return lab
 
     def ldd(self, delta, opt=None):
         d = np.ascontiguousarray(delta, dtype=np.float64)
