@@ -63,6 +63,9 @@ WORKLOADS = {
                        desc="low-diameter decomposition (Alg. 6), beta 0.2, shifts seeded "
                             "(graphgen.exp_shifts, seed 5), RMAT scale 22 ef16; one step = one "
                             "decomposition; GTEPS = undirected edges / time"),
+    "cc-rmat22": dict(kind="cc", graph="rmat", scale=22, ef=16, w=None, nsrc=1,
+                      desc="connected components (smallest-id labels), RMAT scale 22 ef16; one "
+                           "step = one labelling; GTEPS = undirected edges / time"),
     "wbfs-rmat26": dict(kind="wbfs", graph="rmat", scale=26, ef=16, w=(1, 22), nsrc=2,
                         desc="wBFS, RMAT scale 26 ef16, w in [1,22), 2 seeded sources"),
     "msbfs-rmat24": dict(kind="msbfs", graph="rmat", scale=24, ef=16, w=None, nsrc=64,
@@ -128,7 +131,7 @@ def make_sources(g, wl, rank=0):
 
 
 ORACLE_NAME = {"bfs": "FIFO BFS", "wbfs": "binary-heap Dijkstra", "delta": "binary-heap Dijkstra",
-               "ldd": "MPX rounds",
+               "ldd": "MPX rounds", "cc": "FIFO search per component",
                "bf": "frontier Bellman-Ford", "widest": "(max,min) Bellman-Ford rounds",
                "bc": "betweenness forward + backward passes", "kcore": "bucket peeling"}
 
@@ -213,6 +216,7 @@ KERNEL_SOURCES = {
     "bc_kernel": ("betweenness.cu", "dev_common.cuh", "gbf_impl.h"),
     "kcore_kernel": ("kcore.cu", "dev_common.cuh", "gbf_impl.h"),
     "ldd_kernel": ("ldd.cu", "dev_common.cuh", "gbf_impl.h"),
+    "cc_kernel": ("connectivity.cu", "dev_common.cuh", "gbf_impl.h"),
 }
 
 
@@ -257,6 +261,11 @@ def bytes_model(kind, n, st):
         # per successful writeMin: atomicMin and the degree-1 bitmap word (8);
         # per heavy vertex: queue + degree prefix written and read (16)
         return 4 * n + 20 * I + 12 * E + 8 * R + 16 * st["heavy_vertices"]
+    if kind == "cc":
+        # init labels and the queue of vertices with arcs (4n + 12n); per
+        # round every arc: target, both labels (12), and the shortcut pass
+        # over every vertex: its label and the label it names (8n)
+        return 16 * n + 12 * E + st["rounds"] * 8 * n
     if kind == "ldd":
         # read the shifts (8n), write C and T (8n); per round the centre pass
         # reads C and T of every vertex (8n); per frontier vertex its queue
@@ -338,6 +347,9 @@ def cpu_reference_sample(g, wl, srcs, budget_s=15.0, max_queries=None):
             d = np.zeros(g.n, dtype=np.int64)  # every edge is processed
         elif wl["kind"] == "ldd":
             oracle.ldd(g, G.exp_shifts(g.n, wl["beta"], seed=5))
+            d = np.zeros(g.n, dtype=np.int64)
+        elif wl["kind"] == "cc":
+            oracle.components(g)
             d = np.zeros(g.n, dtype=np.int64)
         else:
             d, _ = oracle.bfs(g, int(s))
@@ -804,6 +816,8 @@ def main():
             gb.gbf_kcore(graph.h, outs[i], opt, stream)
         elif kind == "ldd":
             gb.gbf_ldd(graph.h, ldd_delta_dev, outs[i], ldd_rounds, opt, stream)
+        elif kind == "cc":
+            gb.gbf_connectivity(graph.h, outs[i], opt, stream)
         else:
             gb.gbf_bfs(graph.h, int(srcs[i]), outs[i], pars[i], opt, stream)
 
@@ -814,7 +828,7 @@ def main():
             launch(i)
             if w == 0:
                 stats.append(gb.gbf_wait(graph.h, stream))
-                if kind in ("kcore", "ldd"):
+                if kind in ("kcore", "ldd", "cc"):
                     te.append(g.m // 2)
                 elif kind == "bc":
                     # the component, from one untimed BFS of this library
@@ -892,6 +906,8 @@ def main():
                 gb.gbf_kcore(graph.h, host_out[i], opt, None)
             elif kind == "ldd":
                 gb.gbf_ldd(graph.h, ldd_delta, host_out[i], host_rounds, opt, None)
+            elif kind == "cc":
+                gb.gbf_connectivity(graph.h, host_out[i], opt, None)
             else:
                 gb.gbf_bfs(graph.h, int(srcs[i]), host_out[i], host_par[i], opt, None)
     e2e_s = time.perf_counter() - t0
