@@ -93,3 +93,19 @@ def test_serve_cpu_tasks_run_the_oracle():
 def test_host_cpu_names_model_and_cores():
     h = bench.host_cpu()
     assert h["nproc"] == os.cpu_count() and isinstance(h["model"], str) and h["model"]
+
+
+def test_every_workload_has_an_oracle_leg():
+    """The reference arm and the CPU baseline run the oracle for every kind
+    of workload: each one answers on a tiny graph of the same kind."""
+    import graphgen as G
+    kinds = {wl["kind"] for wl in bench.WORKLOADS.values()} - {"serve", "msbfs"}
+    for kind in kinds:
+        wl = next(w for w in bench.WORKLOADS.values() if w["kind"] == kind)
+        g = G.rmat(8, 8, seed=3)
+        if wl["w"] is not None:
+            G.add_weights(g, wl["w"][0], wl["w"][1], seed=2)
+        srcs = G.sources(g, 2, seed=3)
+        te, t, q = bench.cpu_reference_sample(g, wl, srcs, budget_s=5.0, max_queries=1)
+        assert q == 1 and te > 0 and t >= 0, kind
+        assert kind in bench.ORACLE_NAME, kind
