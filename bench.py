@@ -1,17 +1,26 @@
 #!/usr/bin/env python3
 """Benchmark of the frontier-traversal path on one GB300 (or N replicas).
 
-Default workload (the configuration the headline metric is quoted on):
-weighted BFS (integral-weight SSSP) on a seeded RMAT graph, scale 22, edge
-factor 16, a/b/c/d = .57/.19/.19/.05, symmetrized and deduplicated, uint32
-weights uniform in [1, 22); 8 seeded sources run one at a time.  One step =
-those 8 queries.  Other workloads: --workload bfs-rmat22, bfs-rmat26,
-wbfs-rmat26, bfs-grid, wbfs-grid.
+Default workload (the largest single-GPU configuration, the one the HBM
+roofline target is set on): BFS with distances and parents on a seeded RMAT
+graph, scale 26 (67,108,864 vertices, ~2.1 B arcs), edge factor 16,
+a/b/c/d = .57/.19/.19/.05, symmetrized and deduplicated; 4 seeded sources
+run one at a time.  One step = those 4 queries.  Other workloads:
+--workload wbfs-rmat22, bfs-rmat22, wbfs-rmat26, bfs-grid, wbfs-grid,
+msbfs-rmat24, serve, and the next rows' kernels.
 
 Metric: GTEPS, Graph500 convention: per query, the undirected edges of the
 reached component (sum of reached degrees / 2), summed over queries, over the
-device time.  The graph (~1 GB at scale 22) is larger than L2, so no flush
-is needed between steps.
+device time.  The graph (8.4 GB of targets at scale 26) is larger than L2,
+so no flush is needed between steps.
+
+Roofline: algorithmic bytes per launch from the query's device counters
+(4 B per scanned arc, 8 per expanded frontier vertex, 4 per dense-round
+candidate, 12 per reached vertex, 4 per queue read, two bitmap passes per
+dense round, 8 n for the initialisation; weighted BFS counts 8 B per arc and
+4 B per bucket write and read) over the CUDA-event time of the launch;
+a richer model that also counts the per-arc distance and bitmap reads is
+reported beside it as `extended`.
 
 Prints ONE JSON line.  --impl reference times the oracle (the serial CPU
 reference) on bounded samples of the same workload instead.
@@ -130,7 +139,7 @@ def make_sources(g, wl, rank=0):
     return G.sources(g, k, seed=3 + 1000 * rank)
 
 
-ORACLE_NAME = {"bfs": "FIFO BFS", "wbfs": "binary-heap Dijkstra", "delta": "binary-heap Dijkstra",
+ORACLE_NAME = {"bfs": "FIFO BFS", "msbfs": "FIFO BFS per source", "wbfs": "binary-heap Dijkstra", "delta": "binary-heap Dijkstra",
                "ldd": "MPX rounds", "cc": "FIFO search per component",
                "bf": "frontier Bellman-Ford", "widest": "(max,min) Bellman-Ford rounds",
                "bc": "betweenness forward + backward passes", "kcore": "bucket peeling"}
@@ -246,8 +255,34 @@ def measured_traffic(workload, kernel):
     return e.get("bytes_per_launch")
 
 
+def bytes_algorithmic(kind, n, st, lanes=64):
+    """Algorithmic bytes of one query for the traversal kernels, from the
+    query's device counters: E arcs scanned, Vx frontier vertices expanded
+    (each read from its queue), Vp dense-round candidates, R vertices
+    reached, Dn dense rounds, I bucket filings.  Random accesses count their
+    own bytes, not a 32 B sector.  None for kernels without such a model."""
+    E, Vx, Vp = st["edges_scanned"], st["vertices_expanded"], st.get("vertices_pulled", 0)
+    R, Dn, I = st["vertices_reached"], st["pull_rounds"], st["bucket_inserts"]
+    nb = (n + 7) // 8
+    if kind == "bfs":
+        # target per arc; offsets pair and queue entry per expanded vertex;
+        # the extra offset of each dense candidate; D, parent and queue entry
+        # per reached vertex; frontier and visited bitmaps per dense round;
+        # D and parent initialised
+        return 4 * E + 8 * Vx + 4 * Vp + 12 * R + 4 * Vx + 2 * nb * Dn + 8 * n
+    if kind in ("wbfs", "delta"):
+        # as BFS with target + weight per arc and no queue reads; every bucket
+        # filing is written once and read once when its bucket is taken
+        return 8 * E + 8 * Vx + 4 * Vp + 12 * R + 8 * I + 2 * nb * Dn + 8 * n
+    if kind == "msbfs":
+        # target and the neighbour's 8-byte lane word per arc; seen, visit and
+        # next (8 B each) per vertex and level; every distance written once
+        return 12 * E + 24 * n * st["rounds"] + 4 * lanes * n
+    return None
+
+
 def bytes_model(kind, n, st):
-    """Algorithmic bytes of one query (every access counted once, 4 B per
+    """Extended bytes of one query (every access counted once, 4 B per
     word, random or not), from the device statistics of the query."""
     E, V, R, I = st["edges_scanned"], st["vertices_expanded"], st["relaxations"], st["bucket_inserts"]
     if kind == "delta":
@@ -307,10 +342,23 @@ def bytes_model(kind, n, st):
         3 * (n // 8) * st["pull_rounds"]
 
 
+ALG_MODEL = {
+    "bfs": "4 E + 8 Vx + 4 Vp + 12 R + 4 Vx + 2 ceil(n/8) Dn + 8 n",
+    "wbfs": "8 E + 8 Vx + 4 Vp + 12 R + 8 I + 2 ceil(n/8) Dn + 8 n",
+    "delta": "8 E + 8 Vx + 4 Vp + 12 R + 8 I + 2 ceil(n/8) Dn + 8 n",
+    "msbfs": "12 E + 24 n L + 4 k n",
+}
+EXT_MODEL = "extended: every access of the kernel counted once at 4 B per word (bench.bytes_model)"
+# device counters the byte models read (E, Vx, Vp, R, Dn, I, L)
+STAT_TERMS = ("edges_scanned", "vertices_expanded", "vertices_pulled", "vertices_reached",
+              "pull_rounds", "bucket_inserts", "rounds")
+
+
 def trace_summary(tr):
     """Per-kind round counts and device time of one query's round trace."""
     out, prev = {}, 0
-    names = {1: "sparse", 2: "dense", 3: "sparse+heavy", 4: "conversion", 5: "bucket"}
+    names = {1: "sparse", 2: "dense", 3: "sparse+heavy", 4: "conversion+sparse", 5: "bucket",
+             6: "sparse-bitmap", 7: "conversion+sparse-bitmap"}
     for (_, kind, fr, fe, t, _tm) in tr:
         k = names.get(kind, str(kind))
         d = out.setdefault(k, {"rounds": 0, "us": 0.0, "frontier": 0})
@@ -439,31 +487,78 @@ def serve_cpu_tasks(csrs, seed):
         yield sssp(csrs[j], s) if rng.random() >= 0.8 else bfs(csrs[j], s)
 
 
+def workload_config(name, wl, g, nsrc):
+    """The `config` object of a bench line: the workload and its sizes (the
+    same keys and values in the GPU arm and the reference arm)."""
+    seeds = {"graph": 1, "sources": 3}
+    if wl["w"] is not None:
+        seeds["weights"] = 2
+    return {"workload": name, "desc": wl["desc"], "n": int(g.n), "arcs": int(g.m),
+            "sources_per_step": int(nsrc), "seeds": seeds,
+            "l2": "inputs larger than L2 (graph arrays exceed 129 MB); no flush"}
+
+
+def serve_config(wl, csrs, rates, warm, meas):
+    return {"workload": "serve", "desc": wl["desc"], "rates": rates,
+            "queries_per_rate": {"warmup": warm, "measured": meas},
+            "graphs": [{"scale": sc, "n": c.n, "arcs": c.m} for sc, c in zip(wl["scales"], csrs)],
+            "arrival_seed": 4}
+
+
+def serve_graphs(wl):
+    csrs = []
+    for sc in wl["scales"]:
+        g = G.rmat(sc, wl["ef"], 0.57, 0.19, 0.19, seed=1, permute=True)
+        G.add_weights(g, wl["w"][0], wl["w"][1], seed=2)
+        csrs.append(g)
+    return csrs
+
+
 def run_reference(args, wl, rank, world):
+    """The reference arm: the oracle as it stands, on the host cores.  Each
+    step is one single-source oracle query of the workload (one decomposition
+    for the whole-graph kernels; one query of the serving mix for `serve`),
+    a bounded sample of the GPU arm's step.  The steps run as independent
+    queries on all host cores (one thread each; the oracle's C calls release
+    the GIL), so that a scale-26 run of the default K and W ends within a
+    few minutes."""
     if rank != 0:
         return 0
-    g = make_graph(wl)
-    srcs = make_sources(g, wl)
-    # each step = one oracle query (a bounded sample of the 8-query step)
-    te_tot, t_tot, q = 0, 0.0, 0
-    for i in range(args.warmup + args.steps):
-        s = srcs[i % len(srcs)]
-        te, t, _ = cpu_reference_sample(g, wl, [s], budget_s=1e9, max_queries=1)
-        if i >= args.warmup:
-            te_tot += te
-            t_tot += t
-            q += 1
-    gteps = te_tot / t_tot / 1e9
-    line = {"metric": "GTEPS", "value": gteps, "unit": "GTEPS", "impl": "reference",
+    threads = max(1, min(os.cpu_count() or 1, args.steps))
+    if wl["kind"] == "serve":
+        csrs = serve_graphs(wl)
+        rates = [int(r) for r in (args.rates.split(",") if args.rates else wl["rates"])]
+        warm, meas = (args.serve_warm or wl["warm"]), (args.serve_meas or wl["meas"])
+        cfg = serve_config(wl, csrs, rates, warm, meas)
+        tasks = serve_cpu_tasks(csrs, seed=7)
+        _, _, _, _ = cpu_parallel_sample((next(tasks) for _ in range(args.warmup)), 1e9, threads)
+        _, q, wall, th = cpu_parallel_sample((next(tasks) for _ in range(args.steps)), 1e9, threads)
+        val, unit, metric = q / wall, "queries/s", "served queries/s"
+        what = f"{q} queries of the serving mix (FIFO BFS / binary-heap Dijkstra)"
+    else:
+        g = make_graph(wl)
+        srcs = make_sources(g, wl)
+        cfg = workload_config(args.workload, wl, g, len(srcs))
+
+        def task(i):
+            s = srcs[i % len(srcs)]
+            return lambda: cpu_reference_sample(g, wl, [s], budget_s=1e9, max_queries=1)[0]
+        cpu_parallel_sample((task(i) for i in range(args.warmup)), 1e9, threads)
+        te, q, wall, th = cpu_parallel_sample((task(args.warmup + i) for i in range(args.steps)),
+                                              1e9, threads)
+        val, unit, metric = te / wall / 1e9, "GTEPS", "GTEPS"
+        what = (f"{q} single-source oracle queries ({ORACLE_NAME[wl['kind']]}), one per step, "
+                f"of the {wl['nsrc']}-source step")
+    line = {"metric": metric, "value": val, "unit": unit, "impl": "reference",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1000.0 * t_tot / max(q, 1), "higher_is_better": True,
+            "ms_per_step": 1000.0 * wall / max(q, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": args.workload, "desc": wl["desc"]},
-            "cpu_baseline": {"value": gteps, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+            "config": cfg,
+            "cpu_baseline": {"value": val, "unit": unit, "cores": th, "kind": "oracle",
                              "host": host_cpu(),
-                             "sample": f"{q} single-source oracle queries (one per step) of the "
-                                       f"{wl['nsrc']}-source step, 1 thread"},
-            "e2e": {"value": gteps, "unit": "GTEPS", "h2d_bytes_per_step": 0,
+                             "sample": f"{what}, run as independent queries on {th} host threads, "
+                                       f"{wall:.1f} s"},
+            "e2e": {"value": val, "unit": unit, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -548,11 +643,7 @@ def run_serve(args, wl, rank, world):
     if rank != 0:
         return 0
     torch.cuda.set_device(0)
-    csrs = []
-    for sc in wl["scales"]:
-        g = G.rmat(sc, wl["ef"], 0.57, 0.19, 0.19, seed=1, permute=True)
-        G.add_weights(g, wl["w"][0], wl["w"][1], seed=2)
-        csrs.append(g)
+    csrs = serve_graphs(wl)
     hs = [gb.Graph(c, validate=gb.VALIDATE_BASIC) for c in csrs]
     rates = [int(r) for r in (args.rates.split(",") if args.rates else wl["rates"])]
     warm, meas = (args.serve_warm or wl["warm"]), (args.serve_meas or wl["meas"])
@@ -589,10 +680,7 @@ def run_serve(args, wl, rank, world):
         "metric": "served queries/s", "value": best, "unit": "queries/s", "n_gpus": 1,
         "steps": len(rates), "warmup": warm, "ms_per_step": None, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": "serve", "desc": wl["desc"], "rates": rates,
-                   "queries_per_rate": {"warmup": warm, "measured": meas},
-                   "graphs": [{"scale": sc, "n": c.n, "arcs": c.m} for sc, c in zip(wl["scales"], csrs)],
-                   "arrival_seed": 4},
+        "config": serve_config(wl, csrs, rates, warm, meas),
         "serve": res,
         "speedup_vs_one_per_launch": best / base,
         "cpu_baseline": cpu,
@@ -667,7 +755,8 @@ def run_msbfs(args, wl, g, srcs, graph, opt, stream, dev, rank, world, barrier, 
     value = te_all * args.steps / (ms_total / 1e3) / 1e9
     launch_ms = [e[0].elapsed_time(e[1]) for e in ev]
     peak, peak_kind = load_peaks()
-    bpl = bytes_model("msbfs", n, stats)
+    bpl = bytes_algorithmic("msbfs", n, stats, lanes=k)
+    bpl_ext = bytes_model("msbfs", n, stats)
     avg = sum(launch_ms) / len(launch_ms)
     # end to end: host output buffer, the 64 x n result copied back each step
     host = torch.empty((k, n), dtype=torch.int32, pin_memory=True).numpy()
@@ -708,9 +797,8 @@ def run_msbfs(args, wl, g, srcs, graph, opt, stream, dev, rank, world, barrier, 
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "uint64-lanes/int32",
             "data": "synthetic",
-            "config": {"workload": args.workload, "desc": wl["desc"], "n": n, "arcs": g.m,
-                       "sources_per_step": k, "seeds": {"graph": 1, "sources": 3},
-                       "l2": "inputs larger than L2; no flush", "tuned_options": tuned},
+            "config": workload_config(args.workload, wl, g, k),
+            "options": {"tuned": tuned},
             "vs_single_source_launches": {"ms_64_single": ms_single64,
                                           "ms_one_msbfs": ms_total / args.steps,
                                           "speedup": ms_single64 / (ms_total / args.steps),
@@ -719,8 +807,12 @@ def run_msbfs(args, wl, g, srcs, graph, opt, stream, dev, rank, world, barrier, 
             "roofline": {"bound": "hbm", "kernel": "msbfs_kernel", "achieved": bpl / (avg / 1e3) / 1e9,
                          "peak": peak, "unit": "GB/s", "frac": bpl / (avg / 1e3) / 1e9 / peak,
                          "peak_source": f"{peak_kind} hbm_gbs (burst copy)", "bytes_per_launch": bpl,
-                         "avg_launch_ms": avg,
-                         "traffic": measured_traffic(args.workload, "msbfs_kernel")},
+                         "avg_launch_ms": avg, "model": ALG_MODEL["msbfs"],
+                         "traffic": measured_traffic(args.workload, "msbfs_kernel"),
+                         "extended": {"bytes_per_launch": bpl_ext,
+                                      "achieved": bpl_ext / (avg / 1e3) / 1e9,
+                                      "frac": bpl_ext / (avg / 1e3) / 1e9 / peak,
+                                      "model": EXT_MODEL}},
             "cpu_baseline": cpu,
             "cpu_baseline_all_cores": cpu_all,
             "e2e": {"value": te_all * e2e_steps / e2e_s / 1e9, "unit": "GTEPS",
@@ -728,6 +820,7 @@ def run_msbfs(args, wl, g, srcs, graph, opt, stream, dev, rank, world, barrier, 
             "gpu_launches": args.steps,
             "clocks": {kk: clocks[kk] for kk in ("sm_mhz", "sm_max_mhz", "reasons")},
             "stats": {"levels": stats["rounds"], "pull_levels": stats["pull_rounds"],
+                      "per_query": [{f: stats[f] for f in STAT_TERMS}],
                       "edges_scanned": stats["edges_scanned"], "traversed_edges_per_step": te_step,
                       "grid_ctas": stats["grid_ctas"], "block": stats["block"],
                       "query0_trace": trace_summary(trace0)},
@@ -745,7 +838,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gbf", choices=["gbf", "reference"])
-    ap.add_argument("--workload", default="wbfs-rmat22", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="bfs-rmat26", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--opt", default="", help="comma list of gbf_options overrides k=v")
@@ -876,10 +969,13 @@ def main():
 
     # Roofline of the one persistent kernel (each query is one launch).
     peak, peak_kind = load_peaks()
-    bytes_per_step = sum(bytes_model(kind, n, s) for s in stats)
     avg_launch_ms = sum(launch_ms) / len(launch_ms)
-    bytes_per_launch = bytes_per_step / len(srcs)
+    ext_per_launch = sum(bytes_model(kind, n, s) for s in stats) / len(srcs)
+    alg = [bytes_algorithmic(kind, n, s) for s in stats]
+    has_alg = all(a is not None for a in alg)
+    bytes_per_launch = sum(alg) / len(srcs) if has_alg else ext_per_launch
     achieved = bytes_per_launch / (avg_launch_ms / 1e3) / 1e9
+    ext_achieved = ext_per_launch / (avg_launch_ms / 1e3) / 1e9
 
     # End to end: the C-ABI call with host buffers (D2H of each result inside).
     host_out = [torch.empty(n, dtype=out_dtype, pin_memory=True).numpy() for _ in srcs]
@@ -937,15 +1033,16 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if kind == "bc" else "int32",
             "data": "synthetic",
-            "config": {"workload": args.workload, "desc": wl["desc"], "n": n, "arcs": g.m,
-                       "sources_per_step": len(srcs), "seeds": {"graph": 1, "weights": 2, "sources": 3},
-                       "l2": "inputs larger than L2 (graph arrays exceed 129 MB); no flush",
-                       "options": {f: getattr(opt, f) for f, _ in opt._fields_}},
+            "config": workload_config(args.workload, wl, g, len(srcs)),
+            "options": {f: getattr(opt, f) for f, _ in opt._fields_},
             "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_source": f"{peak_kind} hbm_gbs (burst copy)",
                          "bytes_per_launch": bytes_per_launch, "avg_launch_ms": avg_launch_ms,
-                         "traffic": measured_traffic(args.workload, kname)},
+                         "model": ALG_MODEL[kind] if has_alg else EXT_MODEL,
+                         "traffic": measured_traffic(args.workload, kname),
+                         "extended": {"bytes_per_launch": ext_per_launch, "achieved": ext_achieved,
+                                      "frac": ext_achieved / peak, "model": EXT_MODEL}},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": "GTEPS",
                     "h2d_bytes_per_step": 8 * n if kind == "ldd" else 4 * len(srcs),
@@ -955,6 +1052,7 @@ def main():
             "stats": {"rounds": [s["rounds"] for s in stats],
                       "pull_rounds": [s["pull_rounds"] for s in stats],
                       "edges_scanned": sum(s["edges_scanned"] for s in stats),
+                      "per_query": [{f: s[f] for f in STAT_TERMS} for s in stats],
                       "traversed_edges_per_step": te_step,
                       "grid_ctas": stats[0]["grid_ctas"], "block": stats[0]["block"],
                       "query0_trace": trace_summary(trace0)},

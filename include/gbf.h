@@ -76,7 +76,9 @@ typedef struct gbf_graph gbf_graph;
  *                 out-degree sum exceeds m / pull_divisor (default 20; -1 = push only)
  *   heavy_cutoff  largest number of frontier edges one CTA processes as one
  *                 block of the blocked sparse edgeMap; a vertex with more
- *                 edges is split over several CTAs (power of two, 256..4096; 0 = per-query
+ *                 edges is split over several CTAs (power of two, 256..16384; values whose
+ *                 shared-memory footprint does not fit a CTA with the chosen block give
+ *                 GBF_ERR_INVALID; 0 = per-query
  *                 default: 1024 for multi-source BFS, 512 for BFS and wBFS, whose
  *                 light vertices (<= heavy_cutoff / 8 arcs) are expanded without it)
  *   bucket_window number of open buckets nB of the wBFS bucket structure
@@ -92,6 +94,9 @@ typedef struct gbf_graph gbf_graph;
  *                 128 for BFS, 8 for multi-source BFS)
  *   inject_wait   fault injection for tests: 1 = one CTA waits on a flag nothing sets,
  *                 so the first grid barrier times out and the call returns GBF_ERR_TIMEOUT
+ *   pull_stay     BFS: after a dense level the next level stays dense while its frontier
+ *                 holds more than n / pull_stay vertices (0 = default 24; negative = off,
+ *                 the out-degree rule alone)
  */
 typedef struct {
   int32_t block;
@@ -104,7 +109,7 @@ typedef struct {
   int32_t ctas;
   int32_t pull_serial;
   int32_t inject_wait;
-  int32_t reserved;
+  int32_t pull_stay;
 } gbf_options;
 
 /* Per-query statistics, filled by gbf_wait / host-memory calls. */
@@ -119,6 +124,7 @@ typedef struct {
   int64_t bucket_inserts;    /* wBFS: entries appended to buckets (incl. overflow) */
   int64_t refills;           /* wBFS: overflow-bucket refills */
   int64_t heavy_vertices;    /* frontier vertices expanded by the blocked edgeMap pass */
+  int64_t vertices_pulled;   /* dense rounds: unvisited candidates examined */
   int32_t grid_ctas;         /* CTAs of the persistent launch */
   int32_t block;             /* threads per CTA */
   int32_t device_error;      /* gbf_status reported by the device */
@@ -332,7 +338,7 @@ gbf_status gbf_msbfs(gbf_graph *g, const int32_t *srcs, int32_t k, int32_t *dist
  * §6.2) for queries of `kind` on g, by timing real queries (median of
  * repeats over seeded sources) in a coordinate descent over block in
  * {128, 256, 512, 1024}, divisor in {10, 14, 20, 28, 40} and heavy cutoff in
- * {256, ..., 4096}.  Writes the fastest setting to *out (other fields at
+ * {256, ..., 16384}.  Writes the fastest setting to *out (other fields at
  * their defaults).  Results are cached per (graph fingerprint, device, kind)
  * in the process, and across processes in the file named by the environment
  * variable GBF_TUNE_CACHE if set.  Distances never depend on the knobs.
@@ -422,8 +428,10 @@ gbf_status gbf_server_destroy(gbf_server *s);
 /* One record per round of the last query (see gbf_trace). */
 typedef struct {
   int32_t round;          /* 1-based round (BFS level or wBFS bucket round) */
-  int32_t kind;           /* 1 sparse, 2 dense, 3 sparse + heavy pass, 4 conversion,
-                             5 k-core bucket pass (frontier = the bucket) */
+  int32_t kind;           /* 1 sparse, 2 dense, 3 sparse + heavy pass, 4 conversion
+                             (BFS: bitmap -> queue, then sparse), 5 k-core bucket pass
+                             (frontier = the bucket), 6 BFS sparse level writing a
+                             bitmap, 7 the same after a bitmap -> queue conversion */
   uint32_t frontier;      /* frontier vertices (wBFS: bucket entries, stale ones included) */
   uint32_t frontier_edges;/* out-degree sum of the frontier when known (0 otherwise) */
   int64_t t_ns;           /* device time at the end of the round, since the kernel started */
@@ -445,23 +453,28 @@ gbf_status gbf_trace(gbf_graph *g, gbf_round_trace *out, int32_t cap, int32_t *c
  * by another allocator (a framework's caching allocator, a fixed-budget
  * deployment), or a latency-critical loop where cudaMalloc / cudaFree, which
  * may synchronise the whole device, are not acceptable.  The paper has no
- * counterpart; it is a packaging of the BFS of Alg. 1.
+ * counterpart.
  *   n, m      vertices (1 <= n <= 1,048,576) and arcs (m <= 33,554,432)
- *   off, tgt  the symmetric CSR graph in DEVICE memory (uint32[n+1], int32[m])
+ *   off, tgt  the symmetric CSR graph in DEVICE memory: off holds n+1 uint32
+ *             entries, tgt holds m int32 entries (the caller guarantees these
+ *             lengths; the library cannot see them)
  *   src       source vertex
  *   dist      int32[n] in device memory (GBF_INF if unreachable)
  *   parent    int32[n] in device memory, or NULL
  *   opt       NULL for defaults
  *   cuda_stream  stream to run on; the call blocks until the search is done
  *             and returns the device-side status
- * The call allocates nothing: its scratch (~26.7 MB) is one fixed array in
- * the library's device module, held on every GPU that loads the library
- * until the process exits.  The first call on a device looks up that array's
- * device address (cudaGetSymbolAddress) with the device current; make that
- * first call before any stream capture.  All calls share the one array, so
- * calls that overlap on the GPU (different streams, threads or processes
- * sharing a context) race and must be serialised by the caller.  Sizes above
- * the limits return GBF_ERR_INVALID without touching the GPU.
+ * Before the search the call checks the CSR on the device (off[0] = 0,
+ * off[n] = m, offsets non-decreasing, targets in [0, n)) and returns
+ * GBF_ERR_INVALID if it is malformed.  The call allocates nothing: its
+ * scratch (~26.7 MB) is one fixed array in the library's device module, held
+ * on every GPU that loads the library until the process exits.  Every call
+ * looks up that array's device address (cudaGetSymbolAddress) with the device
+ * current; the first call on a device may also load the module, so make it
+ * before any stream capture.  All calls share the one array, so calls that
+ * overlap on the GPU (different streams, threads or processes sharing a
+ * context) race and must be serialised by the caller.  Sizes above the limits
+ * return GBF_ERR_INVALID without touching the GPU.
  */
 gbf_status gbf_bfs_noalloc(int32_t n, uint32_t m, const uint32_t *off, const int32_t *tgt,
                            int32_t src, int32_t *dist, int32_t *parent, const gbf_options *opt,

@@ -42,7 +42,7 @@ class gbf_options(ctypes.Structure):
                 ("dense_wbfs", ctypes.c_int32), ("counters", ctypes.c_int32),
                 ("spin_cap_us", ctypes.c_int64), ("ctas", ctypes.c_int32),
                 ("pull_serial", ctypes.c_int32), ("inject_wait", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("pull_stay", ctypes.c_int32)]
 
 
 class gbf_stats(ctypes.Structure):
@@ -51,7 +51,7 @@ class gbf_stats(ctypes.Structure):
                 ("vertices_expanded", ctypes.c_int64), ("vertices_reached", ctypes.c_int64),
                 ("relaxations", ctypes.c_int64), ("bucket_inserts", ctypes.c_int64),
                 ("refills", ctypes.c_int64), ("heavy_vertices", ctypes.c_int64),
-                ("grid_ctas", ctypes.c_int32),
+                ("vertices_pulled", ctypes.c_int64), ("grid_ctas", ctypes.c_int32),
                 ("block", ctypes.c_int32), ("device_error", ctypes.c_int32),
                 ("reserved", ctypes.c_int32)]
 
@@ -319,9 +319,27 @@ def gbf_trace(h: int, cap: int = 1 << 16) -> list:
             for r in buf[:cnt.value]]
 
 
+def _check_device_i32(name, t, count):
+    """A contiguous CUDA tensor of 4-byte integers holding at least count entries."""
+    if not hasattr(t, "is_cuda") or not t.is_cuda:
+        raise ValueError(f"gbf_bfs_noalloc: {name} must be a CUDA tensor")
+    if t.element_size() != 4 or t.dtype.is_floating_point:
+        raise ValueError(f"gbf_bfs_noalloc: {name} must hold 32-bit integers")
+    if t.numel() < count:
+        raise ValueError(f"gbf_bfs_noalloc: {name} holds {t.numel()} entries, needs {count}")
+
+
 def gbf_bfs_noalloc(n: int, m: int, off, tgt, src: int, dist, parent=None,
                     opt: Optional[gbf_options] = None, stream=None) -> None:
-    """BFS on a caller-held device CSR with no device allocation (blocks)."""
+    """BFS on a caller-held device CSR with no device allocation (blocks).
+    The buffers' lengths are checked here against n and m, since the C call
+    cannot see them."""
+    if 1 <= int(n) <= (1 << 20) and 0 <= int(m) <= (1 << 25):
+        _check_device_i32("off", off, int(n) + 1)
+        _check_device_i32("tgt", tgt, max(int(m), 1))
+        _check_device_i32("dist", dist, int(n))
+        if parent is not None:
+            _check_device_i32("parent", parent, int(n))
     po, mo = _ptr(off)
     pt, mt = _ptr(tgt)
     pd, md = _ptr(dist)

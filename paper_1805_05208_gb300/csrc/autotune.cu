@@ -176,11 +176,11 @@ extern "C" gbf_status gbf_autotune(gbf_graph *h, int32_t kind, gbf_options *out)
   if (s == GBF_OK) {
     const int blocks[] = {128, 256, 512, 1024};
     const int divisors[] = {10, 14, 20, 28, 40};
-    const int heavies[] = {256, 512, 1024, 2048, 4096};
+    const int heavies[] = {256, 512, 1024, 2048, 4096, 8192, 16384};
     for (int pass = 0; pass < 2 && s == GBF_OK; pass++) {
       for (int dim = 0; dim < 3 && s == GBF_OK; dim++) {
         const int *vals = dim == 0 ? blocks : dim == 1 ? divisors : heavies;
-        const int nv = dim == 0 ? 4 : 5;
+        const int nv = dim == 0 ? 4 : dim == 1 ? 5 : 7;
         for (int i = 0; i < nv; i++) {
           gbf_options c = best;
           if (dim == 0) c.block = vals[i];

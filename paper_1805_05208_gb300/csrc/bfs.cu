@@ -3,13 +3,31 @@
 // per level.  Each level runs Ligra's edgeMap (§3) in one of two directions:
 //   - sparse (push): the blocked edgeMap of §6.2 over a frontier queue;
 //     Update is a test-and-set on the visited bitmap (atomicOr) and the winner
-//     writes D[v] = level and parent[v] = u (Alg. 1 Update);
+//     records its parent (Alg. 1 Update);
 //   - dense (pull): every unvisited vertex scans its neighbours in CSR order
 //     and stops at the first one in the frontier bitmap (the early-exit dense
 //     method of §3), writing its bit of the next frontier.
 // The direction is chosen per level from the frontier's out-degree sum:
 // dense when it exceeds m / pull_divisor (§3 "based on the number of edges
-// incident to the current frontier").
+// incident to the current frontier"); after a dense level the next one stays
+// dense while the frontier holds more than n / pull_stay vertices.
+//
+// Layout of the per-level output.  A level whose frontier is large (every
+// dense level, and a sparse level with at least bulk_min frontier edges)
+// writes its new vertices as a bitmap, one of jmax kept for the whole query;
+// their distances are not written during the traversal but by one coalesced
+// pass at the end, which reads each vertex's level from those bitmaps, so the
+// scattered 4-byte writes of D disappear.  Small sparse levels write D
+// directly and hand the next level a compact queue with its degree prefix.
+// The next level converts between the two forms when its direction needs the
+// other one.
+//
+// Graph-side arrays used when the graph provides them: a bitmap of the
+// vertices of degree 0 (they start out visited, so no dense level looks at
+// them) and the target of every vertex's first arc (`f1`): the dense step
+// checks that arc from a coalesced stream before it touches the vertex's
+// adjacency list, which is the sequential scan's first step read from a
+// copy.
 //
 // Readings of Alg. 1 used here: the source is marked visited with D = 0 and
 // vertices first reached while expanding level k-1 get D = k.  A vertex of
@@ -25,13 +43,19 @@
 namespace gbf {
 using namespace dev;
 
+constexpr int kMaxDeferred = 16;  // bitmaps of levels whose D is written at the end
+
 struct BfsParams {
   DevGraph g;
+  const uint32_t *iso;  // bit v set iff deg(v) == 0 (nullable)
+  const int32_t *f1;    // target of each vertex's first arc (nullable)
   int32_t src;
   int32_t *dist;
   int32_t *parent;
   uint32_t *visited;
-  uint32_t *fbm[3];  // frontier bitmaps: input, output, cleared for the next level
+  uint32_t *lb;       // jmax bitmaps of deferred levels, nwords each
+  int jmax;
+  uint32_t *rb[3];    // rotating bitmaps: converted queues, levels written directly
   int32_t *q[2];
   uint32_t *qoff[2];
   uint32_t *qadj[2];
@@ -41,9 +65,10 @@ struct BfsParams {
   TraceRec *trace;
   int trace_cap;
   int pull_divisor;
-  int log2_bmax_fine;  // log2(Bmax / 256)
+  int pull_stay;      // > 0: stay dense while |F| * pull_stay > n
+  uint32_t bulk_min;  // frontier edges from which a sparse level writes a bitmap
   int bmax;
-  int cap;             // staging capacity
+  int cap;            // staging capacity
   int pull_serial;
   int inject_wait;
   long long cap_ns;
@@ -51,9 +76,10 @@ struct BfsParams {
 
 namespace {
 
-// Sparse-direction Update of Alg. 1: test-and-set on the visited bit; the
-// winner writes D and the parent.  kU windows at a time: all target loads,
-// then all bitmap loads, then the test-and-sets, then the winners' degrees.
+// Sparse-direction Update of Alg. 1 for small frontiers: test-and-set on the
+// visited bit; the winner writes D and the parent and is appended to the next
+// queue.  kU windows at a time: all target loads, then all bitmap loads, then
+// the test-and-sets, then the winners' degrees.
 struct BfsPushFn {
   static constexpr int kWin = kU;  // windows per walk step
   template <class Sink>
@@ -102,18 +128,91 @@ struct BfsPushFn {
   }
 };
 
+// Sparse-direction Update for large frontiers: the winner records its parent
+// and sets its bit of the output bitmap (a reduction, nothing waits for it);
+// D is written directly only when the level has no deferred bitmap.  The
+// winner's offsets are loaded for the next level's frontier size and degree
+// sum and are only used one walk step later, so their round trip overlaps
+// the next step's loads.
+struct BfsBulkPushFn {
+  static constexpr int kWin = kU;
+  const uint32_t *off;
+  const int32_t *tgt;
+  uint32_t *visited;
+  uint32_t *fout;
+  int32_t *dist;  // NULL: the level's D is written by the final pass
+  int32_t *parent;
+  int32_t level;
+  unsigned long long reached;
+  uint32_t cnt, deg;  // this thread's new vertices of degree >= 2 and their degree sum
+  uint32_t pa[kWin], pz[kWin];
+
+  __device__ __forceinline__ void consume() {
+#pragma unroll
+    for (int r = 0; r < kWin; r++) {
+      const uint32_t d = pz[r] - pa[r];
+      if (d >= 2) {
+        cnt++;
+        deg += d;
+      }
+      pa[r] = pz[r] = 0;
+    }
+  }
+  template <class Sink>
+  __device__ __forceinline__ void drain(Sink &, PushSmem &) {
+    consume();
+  }
+  template <class Sink>
+  __device__ __forceinline__ void batch(const bool *val, const int32_t *u, const uint32_t *idx,
+                                        Sink &, PushSmem &) {
+    int32_t v[kWin];
+    uint32_t wd[kWin];
+#pragma unroll
+    for (int r = 0; r < kWin; r++) v[r] = val[r] ? __ldg(tgt + idx[r]) : 0;
+#pragma unroll
+    for (int r = 0; r < kWin; r++) wd[r] = val[r] ? visited[v[r] >> 5] : ~0u;
+    consume();  // the previous step's offsets, loaded one step ago
+    bool win[kWin];
+#pragma unroll
+    for (int r = 0; r < kWin; r++) {
+      const uint32_t bit = 1u << (v[r] & 31);
+      win[r] = false;
+      if (!(wd[r] & bit)) win[r] = !(atomicOr(visited + (v[r] >> 5), bit) & bit);
+    }
+#pragma unroll
+    for (int r = 0; r < kWin; r++) {
+      if (win[r]) {
+        if (parent) parent[v[r]] = u[r];
+        if (dist) dist[v[r]] = level;
+        atomicOr(fout + (v[r] >> 5), 1u << (v[r] & 31));  // result unused: a reduction
+        pa[r] = __ldg(off + v[r]);
+        pz[r] = __ldg(off + v[r] + 1);
+        reached++;
+      }
+    }
+  }
+};
+
+// Sink of the bulk push: nothing is staged; chunk_end keeps the barrier that
+// protects the shared chunk arrays between pieces.
+struct NullSink {
+  __device__ __forceinline__ void chunk_end(PushSmem &) { __syncthreads(); }
+};
+
 // Dense direction (the early-exit pull of §3) as one stream of candidates per
 // warp.  Warps take chunks of kChunkWords bitmap words from a global counter;
-// a word group (kGroupWords words: visited word and the offsets of every
-// vertex) is loaded one step before it is needed and its candidates
-// (unvisited, degree > 0) are appended to the warp's ring in shared memory.
-// Every step each lane checks the next 4 arcs of its candidate in CSR order
-// and takes a new candidate from the ring as soon as its own resolves, so no
-// lane waits for another except at the end of the level.  A candidate still
-// unresolved after `pull_serial` arcs is parked in the lane (a lane whose
-// slot is taken keeps scanning its candidate itself); once kWalkLanes lanes
-// hold one, the warp walks the remaining arcs of all parked candidates
-// together (pull_walk_parked), 128 arcs per step.  Words are owned by one warp, whose
+// a word group (kGroupWords words: visited words, the offsets of every vertex
+// and, with f1, the target of every vertex's first arc) is loaded one step
+// before it is needed.  A candidate (unvisited, degree > 0) whose first arc
+// leads into the frontier is found at once; the others are appended to the
+// warp's ring in shared memory with the rest of their list.  Every step each
+// lane checks the next 4 arcs of its candidate in CSR order and takes a new
+// candidate from the ring as soon as its own resolves, so no lane waits for
+// another except at the end of the level.  A candidate still unresolved after
+// `pull_serial` arcs is parked in the lane (a lane whose slot is taken keeps
+// scanning its candidate itself); once kWalkLanes lanes hold one, the warp
+// walks the remaining arcs of all parked candidates together
+// (pull_walk_parked), 128 arcs per step.  Words are owned by one warp, whose
 // found vertices set their next-frontier and visited bits with one atomicOr
 // per word and step.  The first frontier neighbour in CSR order becomes the
 // parent, as in a sequential early-exit scan.
@@ -126,11 +225,12 @@ constexpr int kWalkLanes = 16;   // parked candidates that start a warp walk
 // fits), and the write of a found vertex's distance and parent.
 struct PullCtx {
   int32_t level;
+  bool direct;  // write D now (else the final pass writes it)
   uint32_t scanned, reached;
   uint32_t cnt, deg;  // found vertices of degree >= 2 and their degree sum
 
   __device__ __forceinline__ void record(const BfsParams &P, int32_t v, int32_t par, uint32_t d) {
-    P.dist[v] = level;
+    if (direct) P.dist[v] = level;
     if (P.parent) P.parent[v] = par;
     reached++;
     if (d >= 2) {
@@ -206,24 +306,24 @@ __device__ __forceinline__ void pull_walk_parked(const BfsParams &P, const uint3
 }
 
 __device__ void pull_level(const BfsParams &P, PushSmem &S, const uint32_t *fin, uint32_t *fout,
-                           uint32_t *fzero, int32_t level, unsigned long long *counter,
+                           bool direct, int32_t level, unsigned long long *counter,
                            unsigned long long &scanned, unsigned long long &reached,
-                           unsigned long long &cand_cnt, int inv) {
+                           unsigned long long &pulled, int inv) {
   const DevGraph &g = P.g;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const uint32_t nwords = ((uint32_t)g.n + 31) >> 5;
-  const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
-  // the bitmap the next dense level writes (nobody reads it in this level)
-  for (uint32_t i = gt; i < nwords; i += gs) fzero[i] = 0u;
   const uint32_t nchunk = (nwords + kChunkWords - 1) / kChunkWords;
   const uint32_t F = (uint32_t)P.pull_serial;
   const unsigned lt = (1u << lane) - 1u;
+  const int32_t *f1 = P.f1;
+  const uint32_t skip = f1 ? 1u : 0u;  // arcs already checked before a candidate enters the ring
   int32_t *rv = S.out_v + warp * kRing;
   uint32_t *rs = S.out_d + warp * kRing, *re = S.pref + warp * kRing;
   uint32_t *scr = S.base + warp * 32;  // per-word bit gathering of one step
   scr[lane] = 0u;
   __syncwarp();
-  PullCtx C{level, 0u, 0u, 0u, 0u};
+  PullCtx C{level, direct, 0u, 0u, 0u, 0u};
+  uint32_t cand_cnt = 0;
   unsigned int *work = &P.ctl->work[inv & 3];
   if (blockIdx.x == 0 && threadIdx.x == 0) st_vol(P.ctl->work[(inv + 2) & 3], 0u);
   const uint32_t twarps = gridDim.x * (uint32_t)nw;
@@ -238,9 +338,10 @@ __device__ void pull_level(const BfsParams &P, PushSmem &S, const uint32_t *fin,
   bool have = false;
   uint32_t pw = 0;
   // the loaded group: offsets of its vertices (pa[r]: word r; the end offset of
-  // a lane's vertex is the next lane's start, pnext after the last word) and
-  // its visited words (lane r holds word r)
+  // a lane's vertex is the next lane's start, pnext after the last word), the
+  // first-arc targets (ph[r]) and its visited words (lane r holds word r)
   uint32_t pa[kGroupWords], pnext = 0, pvis = ~0u;
+  int32_t ph[kGroupWords];
   uint32_t head = 0, tail = 0;
   int32_t cv = -1, pv = -1;
   uint32_t ck = 0, ce = 0, cs0 = 0, pk = 0, pe = 0, ps0 = 0;
@@ -251,6 +352,7 @@ __device__ void pull_level(const BfsParams &P, PushSmem &S, const uint32_t *fin,
     _Pragma("unroll") for (uint32_t r = 0; r < kGroupWords; r++) {                       \
       const uint32_t v = (gw + r) * 32 + lane;                                           \
       pa[r] = v <= (uint32_t)g.n ? __ldg(g.off + v) : 0u;                                \
+      ph[r] = (f1 && v < (uint32_t)g.n) ? __ldg(f1 + v) : -1;                            \
     }                                                                                    \
     {                                                                                    \
       const uint32_t vn = (gw + kGroupWords) * 32;                                       \
@@ -273,8 +375,11 @@ __device__ void pull_level(const BfsParams &P, PushSmem &S, const uint32_t *fin,
 
   if (more) GBF_PULL_PREFETCH();
   while (true) {
-    // append the loaded group's candidates, then start loading the next group
+    // check the loaded group's candidates' first arcs, append the rest to the
+    // ring, then start loading the next group
     if (have && tail - head < kRing - 32 * kGroupWords - 32) {
+      bool cd[kGroupWords];
+      uint32_t za[kGroupWords], fw[kGroupWords];
 #pragma unroll
       for (uint32_t r = 0; r < kGroupWords; r++) {
         const uint32_t vis = __shfl_sync(kFull, pvis, r);
@@ -284,7 +389,26 @@ __device__ void pull_level(const BfsParams &P, PushSmem &S, const uint32_t *fin,
                                                   : pnext;
         if (lane == 31) z = zn;
         const uint32_t v = (pw + r) * 32 + lane;
-        const bool c = v < (uint32_t)g.n && !((vis >> lane) & 1u) && z > a;
+        cd[r] = v < (uint32_t)g.n && !((vis >> lane) & 1u) && z > a;
+        za[r] = z;
+        fw[r] = (f1 && cd[r]) ? fin[(uint32_t)ph[r] >> 5] : 0u;
+      }
+#pragma unroll
+      for (uint32_t r = 0; r < kGroupWords; r++) {
+        const uint32_t a = pa[r], z = za[r];
+        const uint32_t v = (pw + r) * 32 + lane;
+        const bool hit = f1 && cd[r] && ((fw[r] >> (ph[r] & 31)) & 1u);
+        if (cd[r]) {
+          cand_cnt++;
+          C.scanned += skip;
+        }
+        const unsigned hb = __ballot_sync(kFull, hit);
+        if (hit) C.record(P, (int32_t)v, ph[r], z - a);
+        if (hb && lane == 0) {
+          atomicOr(fout + pw + r, hb);
+          atomicOr(P.visited + pw + r, hb);
+        }
+        const bool c = cd[r] && !hit && z - a > skip;
         const unsigned bal = __ballot_sync(kFull, c);
         if (c) {
           const uint32_t i = (tail + __popc(bal & lt)) & (kRing - 1);
@@ -306,9 +430,9 @@ __device__ void pull_level(const BfsParams &P, PushSmem &S, const uint32_t *fin,
       if (r < avail) {
         const uint32_t i = (head + r) & (kRing - 1);
         cv = rv[i];
-        ck = cs0 = rs[i];
+        cs0 = rs[i];
+        ck = cs0 + skip;
         ce = re[i];
-        cand_cnt++;
       }
     }
     head += min((uint32_t)__popc(need), avail);
@@ -377,21 +501,24 @@ __device__ void pull_level(const BfsParams &P, PushSmem &S, const uint32_t *fin,
   if (__any_sync(kFull, pv >= 0)) pull_walk_parked(P, fin, fout, C, pv, pk, pe, ps0);
   scanned += C.scanned;
   reached += C.reached;
+  pulled += cand_cnt;
   unsigned long long packed = ((unsigned long long)C.cnt << 32) | C.deg;
   unsigned long long tot = block_sum64(packed, S.misc64);
   if (threadIdx.x == 0 && tot) atomicAdd(counter, tot);
 }
 
-// Sparse queue -> bitmap fb (cleared first, with the bitmap fo the next
-// dense level writes; two barriers).
+// Grid-stride clear of one bitmap.
+__device__ __forceinline__ void clear_bitmap(uint32_t *b, uint32_t nwords) {
+  const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  for (uint32_t i = gt; i < nwords; i += gs) b[i] = 0u;
+}
+
+// Sparse queue -> bitmap fb (cleared first; two barriers).
 __device__ bool queue_to_bitmap(const BfsParams &P, const int32_t *q, uint32_t cnt, uint32_t *fb,
-                                uint32_t *fo, Barrier &bar, int *s_flag) {
+                                Barrier &bar, int *s_flag) {
   const uint32_t nwords = ((uint32_t)P.g.n + 31) >> 5;
   const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
-  for (uint32_t i = gt; i < nwords; i += gs) {
-    fb[i] = 0u;
-    fo[i] = 0u;
-  }
+  clear_bitmap(fb, nwords);
   if (!grid_sync(P.ctl, bar, s_flag)) return false;
   for (uint32_t i = gt; i < cnt; i += gs) {
     const int32_t v = q[i];
@@ -400,39 +527,126 @@ __device__ bool queue_to_bitmap(const BfsParams &P, const int32_t *q, uint32_t c
   return grid_sync(P.ctl, bar, s_flag);
 }
 
-// Bitmap -> sparse queue with degree prefix (CTA-contiguous word ranges).
-// Each warp takes 2 kU words per step with all their loads in flight; the
-// staging area holds one step of the whole CTA (2 kU entries per thread, the
-// staging capacity), so it is flushed between steps whenever it is not empty.
-__device__ void bitmap_to_queue(const BfsParams &P, const uint32_t *fb, PushSmem &S,
-                                const QueueOut &out) {
-  constexpr int R = 2 * kU;
-  const uint32_t nwords = ((uint32_t)P.g.n + 31) >> 5;
-  const uint32_t per = (nwords + gridDim.x - 1) / gridDim.x;
-  const uint32_t wlo = min(nwords, blockIdx.x * per), whi = min(nwords, wlo + per);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (uint32_t base = wlo; base < whi; base += R * nw) {
-    uint32_t a[R], z[R];
-    bool set[R];
-#pragma unroll
-    for (int r = 0; r < R; r++) {
-      const uint32_t wi = base + warp + r * nw;
-      const uint32_t bits = (wi < whi) ? fb[wi] : 0u;
-      set[r] = (bits >> lane) & 1u;
-      const int32_t v = (int32_t)(wi * 32 + lane);
-      a[r] = set[r] ? __ldg(P.g.off + v) : 0u;
-      z[r] = set[r] ? __ldg(P.g.off + v + 1) : 0u;
+// Bitmap -> sparse queue with degree prefix, first-arc offsets and chunk
+// starts, warp by warp over blocks of 32 words (1,024 vertices): a block
+// with no bit set costs one coalesced load; otherwise the warp counts the
+// block's entries (set bits of degree >= 2) and their degrees, reserves its
+// queue and edge range with one 64-bit atomicAdd, and writes the entries.
+// No CTA barrier: warps finish their blocks independently.
+__device__ void bitmap_to_queue(const BfsParams &P, const uint32_t *fb, const QueueOut &out) {
+  const DevGraph &g = P.g;
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const uint32_t nwords = ((uint32_t)g.n + 31) >> 5;
+  const uint32_t nblk = (nwords + 31) >> 5;
+  const uint32_t gwarp = blockIdx.x * (uint32_t)nw + (threadIdx.x >> 5);
+  const uint32_t twarps = gridDim.x * (uint32_t)nw;
+  const unsigned lt = lanemask_lt();
+  for (uint32_t blk = gwarp; blk < nblk; blk += twarps) {
+    const uint32_t wi = blk * 32 + lane;
+    const uint32_t bits = wi < nwords ? fb[wi] : 0u;
+    const unsigned nz = __ballot_sync(kFull, bits != 0u);
+    if (nz == 0u) continue;
+    // pass 1: entries and degree sum of every word (lane i keeps word i's)
+    uint32_t wc = 0, wdg = 0;
+    for (unsigned mm = nz; mm; mm &= mm - 1) {
+      const int i = __ffs(mm) - 1;
+      const uint32_t bw = __shfl_sync(kFull, bits, i);
+      const uint32_t v = (blk * 32 + i) * 32 + lane;
+      const bool set = (bw >> lane) & 1u;
+      const uint32_t a = set ? __ldg(g.off + v) : 0u, z = set ? __ldg(g.off + v + 1) : 0u;
+      const bool e = set && z - a >= 2;
+      const uint32_t c = __popc(__ballot_sync(kFull, e));
+      const uint32_t s = __reduce_add_sync(kFull, e ? z - a : 0u);
+      if (lane == i) {
+        wc = c;
+        wdg = s;
+      }
     }
+    // exclusive prefix over words; one reservation for the block
+    uint32_t ic = wc, id = wdg;
 #pragma unroll
-    for (int r = 0; r < R; r++) {
-      const uint32_t wi = base + warp + r * nw;
-      const uint32_t d = z[r] - a[r];
-      stage_append(S, set[r] && d >= 2, (int32_t)(wi * 32 + lane), d, a[r]);
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t yc = __shfl_up_sync(kFull, ic, o), yd = __shfl_up_sync(kFull, id, o);
+      if (lane >= o) {
+        ic += yc;
+        id += yd;
+      }
     }
-    __syncthreads();
-    stage_make_room(S, out, P.ctl, R * blockDim.x);
+    const uint32_t tc = __shfl_sync(kFull, ic, 31), td = __shfl_sync(kFull, id, 31);
+    if (tc == 0u) continue;
+    unsigned long long old = 0;
+    if (lane == 0) old = atomicAdd(out.counter, ((unsigned long long)tc << 32) | td);
+    old = __shfl_sync(kFull, old, 0);
+    const uint32_t pos = (uint32_t)(old >> 32), dpos = (uint32_t)old;
+    if ((unsigned long long)pos + tc > out.q_cap) {
+      if (lane == 0) raise_error(P.ctl, GBF_ERR_OVERFLOW, 12);
+      continue;
+    }
+    const uint32_t xc = ic - wc, xd = id - wdg;  // exclusive prefixes (lane = word)
+    // pass 2: write the entries (the offsets come back from L1/L2)
+    for (unsigned mm = nz; mm; mm &= mm - 1) {
+      const int i = __ffs(mm) - 1;
+      const uint32_t bw = __shfl_sync(kFull, bits, i);
+      const uint32_t v = (blk * 32 + i) * 32 + lane;
+      const bool set = (bw >> lane) & 1u;
+      const uint32_t a = set ? __ldg(g.off + v) : 0u, z = set ? __ldg(g.off + v + 1) : 0u;
+      const uint32_t d = z - a;
+      const bool e = set && d >= 2;
+      const unsigned eb = __ballot_sync(kFull, e);
+      uint32_t dincl = e ? d : 0u;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(kFull, dincl, o);
+        if (lane >= o) dincl += y;
+      }
+      const uint32_t bxc = __shfl_sync(kFull, xc, i), bxd = __shfl_sync(kFull, xd, i);
+      if (e) {
+        const uint32_t qi = pos + bxc + __popc(eb & lt);
+        const uint32_t e0 = dpos + bxd + dincl - d;
+        out.q[qi] = (int32_t)v;
+        out.qoff[qi] = e0;
+        out.adj[qi] = a;
+        for (uint32_t c = (e0 + kFine - 1) >> kFineLog; (c << kFineLog) < e0 + d; c++)
+          if (c < out.cs_cap) out.cs[c] = qi;
+      }
+    }
   }
-  stage_flush(S, out, P.ctl);
+}
+
+// Distances of the deferred levels, and INF for every vertex never reached,
+// in one coalesced pass; vertices reached in levels that wrote D directly
+// (and the source) keep their value.
+__device__ void final_dist(const BfsParams &P, int jused, const int32_t *s_lvl) {
+  const DevGraph &g = P.g;
+  const uint32_t nwords = ((uint32_t)g.n + 31) >> 5;
+  const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  const uint32_t n4 = ((uint32_t)g.n + 3) >> 2;
+  const bool a16 = ((uintptr_t)P.dist & 15u) == 0;
+  for (uint32_t t = gt; t < n4; t += gs) {
+    const uint32_t v0 = t * 4, w = v0 >> 5, sh = v0 & 31;
+    const uint32_t vis = P.visited[w] & ~(P.iso ? P.iso[w] : 0u);
+    int32_t d[4] = {-2, -2, -2, -2};  // -2: keep
+    for (int j = 0; j < jused; j++) {
+      const uint32_t b = P.lb[(size_t)j * nwords + w] >> sh;
+#pragma unroll
+      for (int k = 0; k < 4; k++)
+        if ((b >> k) & 1u) d[k] = s_lvl[j];
+    }
+    bool all = true;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const uint32_t v = v0 + k;
+      if (d[k] == -2 && v != (uint32_t)P.src && !((vis >> (sh + k)) & 1u)) d[k] = kInf;
+      if (d[k] == -2 || v >= (uint32_t)g.n) all = false;
+    }
+    if (all && a16 && v0 + 3 < (uint32_t)g.n) {
+      *reinterpret_cast<int4 *>(P.dist + v0) = make_int4(d[0], d[1], d[2], d[3]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; k++)
+        if (d[k] != -2 && v0 + k < (uint32_t)g.n) P.dist[v0 + k] = d[k];
+    }
+  }
 }
 
 }  // namespace
@@ -440,6 +654,7 @@ __device__ void bitmap_to_queue(const BfsParams &P, const uint32_t *fb, PushSmem
 __global__ void __launch_bounds__(1024) bfs_kernel(BfsParams P) {
   extern __shared__ unsigned long long smem_raw[];
   __shared__ int s_flag;
+  __shared__ int32_t s_lvl[kMaxDeferred];
   PushSmem S = carve_push_smem(smem_raw, SmemShape{P.bmax, P.cap, 0, 0, 1});
   if (threadIdx.x == 0) S.misc[0] = 0;
   Ctl *ctl = P.ctl;
@@ -448,16 +663,21 @@ __global__ void __launch_bounds__(1024) bfs_kernel(BfsParams P) {
   const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
   const uint32_t nwords = ((uint32_t)g.n + 31) >> 5;
   const int32_t src = P.src;
-  unsigned long long scanned = 0, reached = 0, expanded = 0;
+  unsigned long long scanned = 0, reached = 0, expanded = 0, pulled = 0;
   const unsigned long long t_start = globaltimer();
 
-  // Initialisation (Alg. 1 line 1 and BFS line 1): D = inf, Fl = 0, then the source.
-  for (uint32_t i = gt; i < (uint32_t)g.n; i += gs) {
-    P.dist[i] = (i == (uint32_t)src) ? 0 : kInf;
-    if (P.parent) P.parent[i] = (i == (uint32_t)src) ? src : -1;
+  // Initialisation (Alg. 1): parents -1, the visited
+  // bitmap holds the vertices of degree 0 (never candidates) and the source;
+  // D is written by the final pass or by the level that reaches a vertex.
+  if (P.parent) {
+    const uint32_t n4 = ((uintptr_t)P.parent & 15u) == 0 ? (uint32_t)g.n >> 2 : 0u;
+    for (uint32_t i = gt; i < n4; i += gs)
+      *reinterpret_cast<int4 *>(P.parent + 4 * i) = make_int4(-1, -1, -1, -1);
+    for (uint32_t i = 4 * n4 + gt; i < (uint32_t)g.n; i += gs) P.parent[i] = -1;
   }
   for (uint32_t i = gt; i < nwords; i += gs)
-    P.visited[i] = (i == ((uint32_t)src >> 5)) ? (1u << (src & 31)) : 0u;
+    P.visited[i] = (P.iso ? P.iso[i] : 0u) | ((i == ((uint32_t)src >> 5)) ? (1u << (src & 31)) : 0u);
+  if (P.jmax > 0) clear_bitmap(P.lb, nwords);
   if (blockIdx.x == 0) {
     const uint32_t d0 = __ldg(g.off + src + 1) - __ldg(g.off + src);
     if (threadIdx.x == 0 && d0 > 0) {
@@ -468,36 +688,82 @@ __global__ void __launch_bounds__(1024) bfs_kernel(BfsParams P) {
     }
     for (uint32_t c = threadIdx.x; c < (d0 + kFine - 1) / kFine; c += blockDim.x)
       if (c < P.cs_cap) P.cs[0][c] = 0;
-    if (threadIdx.x == 0) reached = 1;
+    if (threadIdx.x == 0) {
+      reached = 1;
+      P.dist[src] = 0;
+    }
   }
   if (P.inject_wait && blockIdx.x == 0 && threadIdx.x == 0) injected_wait(ctl, P.cap_ns);
   __syncthreads();
+  // the source's parent after the parent initialisation of every CTA
   bool ok = grid_sync(ctl, bar, &s_flag);
+  if (ok && P.parent && blockIdx.x == 0 && threadIdx.x == 0) P.parent[src] = src;
 
-  int fmt_bitmap = 0, qb = 0, fb = 0;
-  int bem = 0;  // blocked edgeMap invocations so far
+  int in_bm = 0;                  // input frontier: 0 = queue q[qb], 1 = bitmap fin
+  const uint32_t *fin = nullptr;
+  int fin_rb = -1;                // rotating bitmap holding fin, or -1
+  int qb = 0, jn = 0, rr = 0, was_dense = 0;
+  int cleared = P.jmax > 0 ? 1 : 0;  // deferred bitmaps cleared so far
+  int bem = 0;  // blocked edgeMap / pull invocations so far
   int level = 1;
   unsigned long long fr = ok ? ld_vol(ctl->fr[0]) : 0ull;
   while (ok) {
-    const uint32_t cnt = (uint32_t)(fr >> 32), D = (uint32_t)fr;
+    uint32_t cnt = (uint32_t)(fr >> 32), D = (uint32_t)fr;
     if (cnt == 0) break;
-    const bool dense =
-        P.pull_divisor > 0 && (unsigned long long)D * (unsigned)P.pull_divisor > g.m;
-    if (dense && !fmt_bitmap) {
-      if (!queue_to_bitmap(P, P.q[qb], cnt, P.fbm[0], P.fbm[1], bar, &s_flag)) break;
-      fmt_bitmap = 1;
-      fb = 0;
-    } else if (!dense && fmt_bitmap) {
-      QueueOut out{P.q[0], P.qoff[0], P.qadj[0], P.cs[0], &ctl->conv, (uint32_t)g.n, P.cs_cap};
-      bitmap_to_queue(P, P.fbm[fb], S, out);
+    bool dense = P.pull_divisor > 0 && (unsigned long long)D * (unsigned)P.pull_divisor > g.m;
+    if (!dense && was_dense && P.pull_divisor > 0 && P.pull_stay > 0 &&
+        (unsigned long long)cnt * (unsigned)P.pull_stay > (unsigned long long)g.n)
+      dense = true;
+    bool converted = false;
+    // the input frontier in the form this direction reads
+    if (!dense && in_bm) {
+      unsigned long long *cv = &ctl->cv[level % 3];
+      QueueOut out{P.q[0], P.qoff[0], P.qadj[0], P.cs[0], cv, (uint32_t)g.n, P.cs_cap};
+      bitmap_to_queue(P, fin, out);
       if (!grid_sync(ctl, bar, &s_flag)) break;
-      fmt_bitmap = 0;
+      const unsigned long long c2 = ld_vol(*cv);
+      cnt = (uint32_t)(c2 >> 32);
+      D = (uint32_t)c2;
+      in_bm = 0;
       qb = 0;
+      fin_rb = -1;
+      converted = true;
+    } else if (dense && !in_bm) {
+      const int x = rr;
+      rr = (rr + 1) % 3;
+      if (!queue_to_bitmap(P, P.q[qb], cnt, P.rb[x], bar, &s_flag)) break;
+      fin = P.rb[x];
+      fin_rb = x;
+      in_bm = 1;
+    }
+    // the output: a deferred bitmap, a rotating bitmap (D written now), or a queue
+    const bool bulk = dense || D >= P.bulk_min;
+    uint32_t *fout = nullptr;
+    bool direct = true;
+    if (bulk) {
+      if (jn < P.jmax) {
+        fout = P.lb + (size_t)jn * nwords;
+        if (threadIdx.x == 0) s_lvl[jn] = level;
+        jn++;
+        direct = false;
+      } else {
+        int x = rr;
+        if (x == fin_rb) x = (x + 1) % 3;
+        rr = (x + 1) % 3;
+        fout = P.rb[x];
+        clear_bitmap(fout, nwords);
+        if (!grid_sync(ctl, bar, &s_flag)) break;
+      }
+    }
+    // clear the deferred bitmap a later level will take
+    if (cleared < P.jmax && cleared <= jn) {
+      clear_bitmap(P.lb + (size_t)cleared * nwords, nwords);
+      cleared++;
     }
     unsigned long long *outc = &ctl->fr[level % 3];
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       st_vol(ctl->fr[(level + 1) % 3], 0ull);
-      st_vol(ctl->conv, 0ull);
+      st_vol(ctl->cv[(level + 1) % 3], 0ull);
       if (dense) atomicAdd(&ctl->pull_rounds, 1);
       else {
         atomicAdd(&ctl->push_rounds, 1);
@@ -506,31 +772,58 @@ __global__ void __launch_bounds__(1024) bfs_kernel(BfsParams P) {
       }
       atomicAdd(&ctl->rounds, 1);
     }
-    if (!fmt_bitmap) {
+    if (!dense) {
       QueueIn in{P.q[qb], P.qoff[qb], P.qadj[qb], P.cs[qb], cnt, D};
-      BfsPushFn fn{g.off, g.tgt, P.visited, P.dist, P.parent, level, 0};
-      StagedSink sink{QueueOut{P.q[qb ^ 1], P.qoff[qb ^ 1], P.qadj[qb ^ 1], P.cs[qb ^ 1], outc,
-                               (uint32_t)g.n, P.cs_cap},
-                      ctl, nullptr};
-      // chunks of one walk step of the whole CTA (kWin 32-edge windows per
-      // warp): a step appends at most half the staging capacity, which
-      // chunk_end keeps free
-      const int s = chunk_shift(D, 4u, chunk_shift_cap(BfsPushFn::kWin * blockDim.x));
-      blocked_edge_map(g, in, s, (uint32_t)P.bmax, S, fn, sink, ctl, bem++);
-      sink.finish(S);
-      reached += fn.reached;
-      qb ^= 1;
+      if (!bulk) {
+        BfsPushFn fn{g.off, g.tgt, P.visited, P.dist, P.parent, level, 0};
+        StagedSink sink{QueueOut{P.q[qb ^ 1], P.qoff[qb ^ 1], P.qadj[qb ^ 1], P.cs[qb ^ 1], outc,
+                                 (uint32_t)g.n, P.cs_cap},
+                        ctl, nullptr};
+        // chunks of one walk step of the whole CTA (kWin 32-edge windows per
+        // warp): a step appends at most half the staging capacity, which
+        // chunk_end keeps free
+        const int s = chunk_shift(D, 4u, chunk_shift_cap(BfsPushFn::kWin * blockDim.x));
+        blocked_edge_map(g, in, s, (uint32_t)P.bmax, S, fn, sink, ctl, bem++);
+        sink.finish(S);
+        reached += fn.reached;
+        qb ^= 1;
+      } else {
+        BfsBulkPushFn fn{g.off, g.tgt, P.visited, fout, direct ? P.dist : nullptr, P.parent,
+                         level, 0, 0u, 0u, {0u, 0u, 0u, 0u}, {0u, 0u, 0u, 0u}};
+        NullSink sink;
+        // nothing is staged, so a chunk may span many walk steps
+        const int s = chunk_shift(D, 4u, 6);
+        blocked_edge_map(g, in, s, (uint32_t)P.bmax, S, fn, sink, ctl, bem++);
+        reached += fn.reached;
+        const unsigned long long packed = ((unsigned long long)fn.cnt << 32) | fn.deg;
+        const unsigned long long tot = block_sum64(packed, S.misc64);
+        if (threadIdx.x == 0 && tot) atomicAdd(outc, tot);
+      }
     } else {
-      pull_level(P, S, P.fbm[fb], P.fbm[(fb + 1) % 3], P.fbm[(fb + 2) % 3], level, outc, scanned,
-                 reached, expanded, bem++);
-      fb = (fb + 1) % 3;
+      pull_level(P, S, fin, fout, direct, level, outc, scanned, reached, pulled, bem++);
     }
     if (!grid_sync(ctl, bar, &s_flag)) break;
     fr = ld_vol(*outc);
-    if (P.trace && blockIdx.x == 0 && threadIdx.x == 0 && level <= P.trace_cap)
-      P.trace[level - 1] = TraceRec{level, fmt_bitmap ? 2 : 1, cnt, D,
-                                    (long long)(globaltimer() - t_start), 0};
+    if (bulk) {
+      in_bm = 1;
+      fin = fout;
+      fin_rb = direct ? (fout == P.rb[0] ? 0 : fout == P.rb[1] ? 1 : 2) : -1;
+    } else {
+      in_bm = 0;
+    }
+    was_dense = dense;
+    if (P.trace && blockIdx.x == 0 && threadIdx.x == 0 && level <= P.trace_cap) {
+      // 1 sparse (queue out), 2 dense, 6 sparse with bitmap out; +1 (1 -> 4,
+      // 6 -> 7) after a bitmap -> queue conversion
+      int kind = dense ? 2 : bulk ? 6 : 1;
+      if (converted) kind = kind == 1 ? 4 : 7;
+      P.trace[level - 1] = TraceRec{level, kind, cnt, D, (long long)(globaltimer() - t_start), 0};
+    }
     level++;
+  }
+  if (ok) {
+    __syncthreads();
+    if (ld_vol(ctl->err) == 0) final_dist(P, jn, s_lvl);
   }
   // statistics
   unsigned long long t;
@@ -540,17 +833,23 @@ __global__ void __launch_bounds__(1024) bfs_kernel(BfsParams P) {
   if (threadIdx.x == 0 && t) atomicAdd(&ctl->reached, t);
   t = block_sum64(expanded, S.misc64);
   if (threadIdx.x == 0 && t) atomicAdd(&ctl->expanded, t);
+  t = block_sum64(pulled, S.misc64);
+  if (threadIdx.x == 0 && t) atomicAdd(&ctl->pulled, t);
 }
 
 gbf_status launch_bfs(Graph &g, Workspace &ws, int32_t src, int32_t *dist, int32_t *parent,
                       const Opts &o, cudaStream_t st) {
   BfsParams P;
   P.g = g.dev();
+  P.iso = g.iso;
+  P.f1 = g.f1;
   P.src = src;
   P.dist = dist;
   P.parent = parent;
   P.visited = ws.visited;
-  for (int i = 0; i < 3; i++) P.fbm[i] = ws.fbm[i];
+  P.lb = ws.lb;
+  P.jmax = ws.lb ? std::min(ws.lb_count, kMaxDeferred) : 0;
+  for (int i = 0; i < 3; i++) P.rb[i] = ws.fbm[i];
   for (int i = 0; i < 2; i++) {
     P.q[i] = ws.q[i];
     P.qoff[i] = ws.qoff[i];
@@ -562,11 +861,10 @@ gbf_status launch_bfs(Graph &g, Workspace &ws, int32_t src, int32_t *dist, int32
   P.trace = ws.trace;
   P.trace_cap = ws.trace_cap;
   P.pull_divisor = o.pull_divisor;
+  P.pull_stay = o.pull_stay;
+  P.bulk_min = std::max<uint32_t>((uint32_t)g.n / 16u, 1u);
   P.bmax = o.heavy_cutoff;
   P.cap = stage_capacity(o.block);
-  int l = 0;
-  while ((kFine << l) < (uint32_t)o.heavy_cutoff) l++;
-  P.log2_bmax_fine = l;
   P.pull_serial = o.pull_serial;
   P.inject_wait = o.inject_wait;
   P.cap_ns = o.spin_cap_ns;

@@ -32,6 +32,7 @@ struct Ctl {
   int stop;                    // fault injection flag nobody sets
   unsigned long long fr[3];    // frontier counters (count << 32 | degree sum), by round % 3
   unsigned long long conv;     // conversion cursor (same packing)
+  unsigned long long cv[3];    // BFS bitmap -> queue conversions (same packing), by level % 3
   // wBFS
   unsigned int mcnt[2];        // moved-list counts, by round parity
   int gmin[3];                 // k-core: smallest remaining degree of the next bucket, by bucket % 3
@@ -47,6 +48,7 @@ struct Ctl {
   unsigned long long relax;
   unsigned long long inserts;
   unsigned long long heavy;
+  unsigned long long pulled;   // dense-round candidates
   int rounds, push_rounds, pull_rounds, refills;
 };
 
@@ -77,6 +79,8 @@ struct Workspace {
   size_t bytes = 0;
   uint32_t *visited = nullptr;   // ceil(n/32) words
   uint32_t *fbm[3] = {nullptr, nullptr, nullptr};
+  uint32_t *lb = nullptr;        // lb_count bitmaps of BFS levels whose D is written at the end
+  int lb_count = 0;
   int32_t *q[2] = {nullptr, nullptr};
   uint32_t *qoff[2] = {nullptr, nullptr};
   uint32_t *qadj[2] = {nullptr, nullptr};  // CSR offset of each entry's first arc
@@ -135,6 +139,8 @@ struct Graph {
   int32_t *tgt = nullptr;
   uint32_t *w = nullptr;
   uint32_t *leaf = nullptr;  // bit v set iff deg(v) == 1 (wBFS does not file these)
+  uint32_t *iso = nullptr;   // bit v set iff deg(v) == 0
+  int32_t *f1 = nullptr;     // target of each vertex's first arc (-1 if it has none)
   size_t bytes = 0;
   Workspace ws;
   std::mutex mu;   // serialises host calls on the default workspace
@@ -144,6 +150,7 @@ struct Graph {
 // Resolved options (defaults filled, clamped).
 struct Opts {
   int block, pull_divisor, heavy_cutoff, bucket_window, dense_wbfs, ctas, pull_serial, inject_wait;
+  int pull_stay;  // BFS: after a dense level, stay dense while |F| * pull_stay > n (0: off)
   long long spin_cap_ns;
 };
 Opts resolve(const gbf_options *o, const Graph &g, int kind);  // kind: GBF_TUNE_*

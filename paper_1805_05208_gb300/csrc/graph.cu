@@ -55,7 +55,7 @@ Opts resolve(const gbf_options *o, const Graph &g, int kind) {
   r.heavy_cutoff = o->heavy_cutoff ? o->heavy_cutoff
                                    : (kind == GBF_TUNE_MSBFS ? 1024 : 512);
   int hc = 256;
-  while (hc < r.heavy_cutoff && hc < 4096) hc <<= 1;
+  while (hc < r.heavy_cutoff && hc < 16384) hc <<= 1;
   r.heavy_cutoff = std::max(hc, r.block);  // staging buffer must hold one CTA pass
   r.bucket_window = o->bucket_window;
   r.dense_wbfs = o->dense_wbfs ? 1 : 0;
@@ -70,6 +70,9 @@ Opts resolve(const gbf_options *o, const Graph &g, int kind) {
   r.pull_serial = o->pull_serial > 0 ? std::min(o->pull_serial, 1 << 20)
                                      : (kind == GBF_TUNE_MSBFS ? 8 : 128);
   r.inject_wait = o->inject_wait ? 1 : 0;
+  // pull_stay 0: default 24 (after a dense level, the next stays dense while
+  // the frontier holds more than n / 24 vertices); negative: off
+  r.pull_stay = o->pull_stay > 0 ? o->pull_stay : (o->pull_stay < 0 ? 0 : 24);
   long long us = o->spin_cap_us > 0 ? o->spin_cap_us : d.spin_cap_us;
   r.spin_cap_ns = us * 1000LL;
   return r;
@@ -164,14 +167,23 @@ __global__ void k_digest(int32_t n, uint32_t m, const uint32_t *off, const int32
   }
 }
 
-// Bit v of leaf[] is set iff vertex v has degree exactly 1.
-__global__ void k_leaf(int32_t n, const uint32_t *off, uint32_t *leaf) {
+// Per-vertex arrays derived from the CSR: bit v of leaf[] is set iff vertex
+// v has degree exactly 1, bit v of iso[] iff it has degree 0, and f1[v] is
+// the target of v's first arc (-1 without arcs).
+__global__ void k_leaf(int32_t n, const uint32_t *off, const int32_t *tgt, uint32_t *leaf,
+                       uint32_t *iso, int32_t *f1) {
   const uint32_t nw = ((uint32_t)n + 31) >> 5;
   const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
   for (uint32_t i = gt; i < nw * 32u; i += gs) {
-    const bool one = i < (uint32_t)n && off[i + 1] - off[i] == 1u;
-    const unsigned b = __ballot_sync(0xffffffffu, one);
-    if ((threadIdx.x & 31) == 0) leaf[i >> 5] = b;
+    const uint32_t a = i < (uint32_t)n ? off[i] : 0u, z = i < (uint32_t)n ? off[i + 1] : 0u;
+    const bool in = i < (uint32_t)n;
+    const unsigned b1 = __ballot_sync(0xffffffffu, in && z - a == 1u);
+    const unsigned b0 = __ballot_sync(0xffffffffu, in && z == a);
+    if ((threadIdx.x & 31) == 0) {
+      leaf[i >> 5] = b1;
+      iso[i >> 5] = b0;
+    }
+    if (in) f1[i] = z > a ? tgt[a] : -1;
   }
 }
 
@@ -206,6 +218,8 @@ gbf_status ws_ensure_base(Graph &g, Workspace &ws) {
   ws.m = g.m;
   GBF_TRY(dmalloc(&ws.visited, nw, acc));
   GBF_TRY(dmalloc(&ws.fbm[2], nw, acc));
+  ws.lb_count = 8;
+  GBF_TRY(dmalloc(&ws.lb, nw * (size_t)ws.lb_count, acc));
   for (int i = 0; i < 2; i++) {
     GBF_TRY(dmalloc(&ws.fbm[i], nw, acc));
     GBF_TRY(dmalloc(&ws.q[i], n, acc));
@@ -320,7 +334,7 @@ gbf_status ws_ensure_bc(Graph &g, Workspace &ws) {
 }
 
 void ws_free(Workspace &ws) {
-  void *ptrs[] = {ws.visited, ws.fbm[0], ws.fbm[1], ws.fbm[2], ws.q[0], ws.q[1], ws.qoff[0], ws.qoff[1],
+  void *ptrs[] = {ws.visited, ws.lb, ws.fbm[0], ws.fbm[1], ws.fbm[2], ws.q[0], ws.q[1], ws.qoff[0], ws.qoff[1],
                   ws.qadj[0], ws.qadj[1], ws.ms_qadj[2],
                   ws.cs[0], ws.cs[1], ws.ctl, ws.dist_tmp, ws.parent_tmp, ws.trace, ws.slots,
                   ws.slot_cnt, ws.ovf[0], ws.ovf[1], ws.ms_seen, ws.ms_visit, ws.ms_next,
@@ -354,6 +368,7 @@ gbf_status ws_collect(Workspace &ws, cudaStream_t st, gbf_stats *stats) {
     stats->bucket_inserts = (int64_t)c.inserts;
     stats->refills = c.refills;
     stats->heavy_vertices = (int64_t)c.heavy;
+    stats->vertices_pulled = (int64_t)c.pulled;
     stats->grid_ctas = ws.last_grid;
     stats->block = ws.last_block;
     stats->device_error = c.err;
@@ -386,6 +401,7 @@ gbf_status gbf_options_default(gbf_options *opt) {
   opt->ctas = 0;
   opt->pull_serial = 0;
   opt->inject_wait = 0;
+  opt->pull_stay = 0;
   return GBF_OK;
 }
 
@@ -435,6 +451,8 @@ gbf_status gbf_graph_create(int32_t n, const uint32_t *off, const int32_t *tgt, 
   if ((s = dmalloc(&g.tgt, (size_t)m, acc)) != GBF_OK) return fail(s);
   if (w && (s = dmalloc(&g.w, (size_t)m, acc)) != GBF_OK) return fail(s);
   if ((s = dmalloc(&g.leaf, ((size_t)n + 31) / 32, acc)) != GBF_OK) return fail(s);
+  if ((s = dmalloc(&g.iso, ((size_t)n + 31) / 32, acc)) != GBF_OK) return fail(s);
+  if ((s = dmalloc(&g.f1, (size_t)n, acc)) != GBF_OK) return fail(s);
   g.bytes = acc;
   const cudaMemcpyKind kind = mem == GBF_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   cudaError_t e;
@@ -470,7 +488,7 @@ gbf_status gbf_graph_create(int32_t n, const uint32_t *off, const int32_t *tgt, 
   }
   if (haux.flags == 0) {
     k_digest<<<grid, 256, 0, st>>>(n, m, g.off, g.tgt, g.w, &aux->sum, &aux->wmax);
-    k_leaf<<<grid, 256, 0, st>>>(n, g.off, g.leaf);
+    k_leaf<<<grid, 256, 0, st>>>(n, g.off, g.tgt, g.leaf, g.iso, g.f1);
   }
   e = cudaStreamSynchronize(st);
   if (e == cudaSuccess) e = cudaMemcpy(&haux, aux, sizeof(Aux), cudaMemcpyDeviceToHost);
@@ -506,6 +524,8 @@ gbf_status gbf_graph_destroy(gbf_graph *h) {
   if (g.tgt) cudaFree(g.tgt);
   if (g.w) cudaFree(g.w);
   if (g.leaf) cudaFree(g.leaf);
+  if (g.iso) cudaFree(g.iso);
+  if (g.f1) cudaFree(g.f1);
   delete h;
   return GBF_OK;
 }

@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(1024) msbfs_kernel(MsParams P) {
   const int k = P.call->k;
   int32_t *const *rows = P.call->rows;
   const u64 ALL = (k >= 64) ? ~0ull : ((1ull << k) - 1ull);
-  unsigned long long scanned = 0, expanded = 0, reached = 0;
+  unsigned long long scanned = 0, expanded = 0, reached = 0, pulled = 0;
   const unsigned long long t_start = globaltimer();
 
   for (uint32_t i = gt; i < n; i += gs) {
@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(1024) msbfs_kernel(MsParams P) {
             reached += __popcll(nwb);
           }
         }
-        if (cand) expanded++;
+        if (cand) pulled++;
         write_rows(rows, k, v, inr ? nwb : 0ull, L);
         stage_append(S, nwb != 0ull && e > s, v, e - s, s);
         __syncthreads();
@@ -353,6 +353,8 @@ __global__ void __launch_bounds__(1024) msbfs_kernel(MsParams P) {
   if (threadIdx.x == 0 && tt) atomicAdd(&ctl->edges_scanned, tt);
   tt = block_sum64(expanded, S.misc64);
   if (threadIdx.x == 0 && tt) atomicAdd(&ctl->expanded, tt);
+  tt = block_sum64(pulled, S.misc64);
+  if (threadIdx.x == 0 && tt) atomicAdd(&ctl->pulled, tt);
   tt = block_sum64(reached, S.misc64);
   if (threadIdx.x == 0 && tt) atomicAdd(&ctl->reached, tt);
 }

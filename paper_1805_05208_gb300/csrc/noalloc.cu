@@ -12,8 +12,6 @@
 // itself allocates nothing.
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "dev_common.cuh"
 #include "gbf_impl.h"
 
@@ -27,30 +25,45 @@ constexpr size_t kBitW = words256((size_t)kMaxN / 32);
 constexpr size_t kQW = words256((size_t)kMaxN);
 constexpr size_t kCsW = words256((size_t)(kMaxM / dev::kFine) + 2);
 constexpr size_t kCtlW = words256((sizeof(Ctl) + 3) / 4);
-constexpr size_t kScratchWords = 4 * kBitW + 6 * kQW + 2 * kCsW + kCtlW;  // ~26.7 MB
+constexpr size_t kFlagW = 64;  // the CSR check's flag word
+constexpr size_t kScratchWords = 4 * kBitW + 6 * kQW + 2 * kCsW + kCtlW + kFlagW;  // ~26.7 MB
 
 static __device__ __align__(256) uint32_t g_scratch[kScratchWords];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-uint32_t *g_scratch_addr[kMaxDevices] = {};
+// The caller's CSR, checked before the search so that a malformed graph is
+// rejected instead of sending the BFS out of bounds: off[0] = 0, off[n] = m,
+// offsets non-decreasing, targets in [0, n).  Every read stays inside off[0..n]
+// and tgt[0..m), whatever the offsets hold.
+__global__ void k_noalloc_check(int32_t n, uint32_t m, const uint32_t *off, const int32_t *tgt,
+                                uint32_t *flag) {
+  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t tw = (gridDim.x * blockDim.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  uint32_t bad = 0;
+  if (gw == 0 && lane == 0 && (off[0] != 0u || off[n] != m)) bad = 1;
+  for (uint32_t v = gw; v < (uint32_t)n; v += tw) {
+    const uint32_t s = off[v], e = off[v + 1];
+    if (e < s || e > m) {
+      bad = 1;
+      continue;
+    }
+    for (uint32_t k = s + lane; k < e; k += 32) {
+      const int32_t t = tgt[k];
+      if (t < 0 || t >= n) bad = 1;
+    }
+  }
+  if (bad) atomicOr(flag, 1u);
+}
 
 // Device address of g_scratch on the current device.  In host code the
 // symbol's name is only a host-side stand-in, so the address is looked up
-// once per device (with that device current) and cached.
-gbf_status scratch_on_device(int dev, uint32_t **out) {
-  if (dev < 0 || dev >= kMaxDevices) {
-    set_error("device ordinal out of range");
-    return GBF_ERR_INVALID;
-  }
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_scratch_addr[dev]) {
-    void *p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_scratch)");
-    g_scratch_addr[dev] = (uint32_t *)p;
-  }
-  *out = g_scratch_addr[dev];
+// with the device current, on every call: a context that was reset and
+// created again may hold the array elsewhere.
+gbf_status scratch_on_device(uint32_t **out) {
+  void *p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_scratch)");
+  *out = (uint32_t *)p;
   return GBF_OK;
 }
 
@@ -81,8 +94,9 @@ extern "C" gbf_status gbf_bfs_noalloc(int32_t n, uint32_t m, const uint32_t *off
   int dev = 0;
   GBF_CUDA(cudaGetDevice(&dev));
   uint32_t *base = nullptr;
-  gbf_status s = scratch_on_device(dev, &base);
+  gbf_status s = scratch_on_device(&base);
   if (s != GBF_OK) return s;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
 
   Graph g;
   g.n = n;
@@ -123,16 +137,30 @@ extern "C" gbf_status gbf_bfs_noalloc(int32_t n, uint32_t m, const uint32_t *off
   ws.cs[1] = p;
   p += kCsW;
   ws.ctl = (Ctl *)p;
+  p += kCtlW;
+  uint32_t *flag = p;
   ws.n = n;
   ws.m = m;
 
+  // the CSR check (its flag word starts at zero on every call)
+  uint32_t bad = 0;
+  GBF_CUDA(cudaMemsetAsync(flag, 0, sizeof(uint32_t), st));
+  k_noalloc_check<<<g.num_sms * 4, 256, 0, st>>>(n, m, off, tgt, flag);
+  GBF_CUDA(cudaGetLastError());
+  GBF_CUDA(cudaMemcpyAsync(&bad, flag, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  GBF_CUDA(cudaStreamSynchronize(st));
+  if (bad) {
+    set_error("gbf_bfs_noalloc: invalid CSR (off[0] != 0, off[n] != m, decreasing offsets or a "
+              "target outside [0, n))");
+    return GBF_ERR_INVALID;
+  }
+
   const Opts o = resolve(opt, g, GBF_TUNE_BFS);
-  cudaStream_t st = (cudaStream_t)cuda_stream;
   s = launch_bfs(g, ws, src, dist, parent, o, st);
   if (s != GBF_OK) return s;
-  GBF_CUDA(cudaStreamSynchronize(st));
   int err = 0;
-  GBF_CUDA(cudaMemcpy(&err, &ws.ctl->err, sizeof(int), cudaMemcpyDeviceToHost));
+  GBF_CUDA(cudaMemcpyAsync(&err, &ws.ctl->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  GBF_CUDA(cudaStreamSynchronize(st));
   if (err != 0) {
     set_error("gbf_bfs_noalloc: device reported an error");
     return (gbf_status)err;

@@ -94,7 +94,7 @@ constexpr int kMaskWords = 8;  // pending / filed slot masks: nB <= 256
 constexpr int32_t kNoSlot = -1;  // a staged entry dropped at the flush (overflow slots are <= -2)
 
 struct Counters {
-  unsigned long long scanned, relax, inserts, expanded, heavy;
+  unsigned long long scanned, relax, inserts, expanded, heavy, pulled;
 };
 
 // Bucket filing, staged per CTA: lanes whose writeMin succeeded reserve a
@@ -366,6 +366,7 @@ __device__ void dense_round(const WbfsParams &P, int32_t b, PushSmem &S, FileSin
       }
     }
     int32_t best = kInf;
+    if (cand) c.pulled++;
     unsigned rm = __ballot_sync(kFull, cand);
     // each candidate's list is scanned by the whole warp, 32 arcs at a time,
     // stopping once the lower bound b + 1 is reached
@@ -449,7 +450,7 @@ __global__ void __launch_bounds__(1024) wbfs_kernel(WbfsParams P) {
   const DevGraph g = P.g;
   const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
   const int32_t src = P.src;
-  Counters c{0, 0, 0, 0, 0};
+  Counters c{0, 0, 0, 0, 0, 0};
   const unsigned long long t_start = globaltimer();
 
   // makeBuckets: D = inf except D[src] = 0; src filed in bucket 0.
@@ -663,6 +664,8 @@ __global__ void __launch_bounds__(1024) wbfs_kernel(WbfsParams P) {
   if (threadIdx.x == 0 && tt) atomicAdd(&ctl->expanded, tt);
   tt = block_sum64(c.heavy, S.misc64);
   if (threadIdx.x == 0 && tt) atomicAdd(&ctl->heavy, tt);
+  tt = block_sum64(c.pulled, S.misc64);
+  if (threadIdx.x == 0 && tt) atomicAdd(&ctl->pulled, tt);
 }
 
 gbf_status launch_wbfs(Graph &g, Workspace &ws, int32_t src, int32_t *dist, const Opts &o,

@@ -109,3 +109,35 @@ def test_every_workload_has_an_oracle_leg():
         te, t, q = bench.cpu_reference_sample(g, wl, srcs, budget_s=5.0, max_queries=1)
         assert q == 1 and te > 0 and t >= 0, kind
         assert kind in bench.ORACLE_NAME, kind
+
+
+def test_bytes_algorithmic_terms():
+    st = dict(edges_scanned=10, vertices_expanded=3, vertices_pulled=7, relaxations=4,
+              bucket_inserts=5, vertices_reached=6, pull_rounds=2, heavy_vertices=2, rounds=4)
+    n = 65
+    nb = (n + 7) // 8
+    assert bench.bytes_algorithmic("bfs", n, st) == \
+        4 * 10 + 8 * 3 + 4 * 7 + 12 * 6 + 4 * 3 + 2 * nb * 2 + 8 * n
+    assert bench.bytes_algorithmic("wbfs", n, st) == \
+        8 * 10 + 8 * 3 + 4 * 7 + 12 * 6 + 8 * 5 + 2 * nb * 2 + 8 * n
+    assert bench.bytes_algorithmic("msbfs", n, st, lanes=64) == 12 * 10 + 24 * n * 4 + 4 * 64 * n
+    assert bench.bytes_algorithmic("kcore", n, st) is None
+    for k in ("bfs", "wbfs", "delta", "msbfs"):
+        assert k in bench.ALG_MODEL
+    assert set(bench.STAT_TERMS) <= set(st) | {"vertices_pulled"}
+
+
+def test_reference_arm_line_has_the_gpu_arms_config(capsys):
+    """The reference arm prints one line whose config is the GPU arm's
+    (same keys, same values) for the same workload."""
+    import argparse
+    wl = dict(kind="bfs", graph="rmat", scale=9, ef=8, w=None, nsrc=3, desc="tiny BFS")
+    args = argparse.Namespace(steps=4, warmup=1, workload="tiny", rates="", serve_warm=0,
+                              serve_meas=0)
+    assert bench.run_reference(args, wl, 0, 1) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    g = bench.make_graph(wl)
+    assert line["config"] == bench.workload_config("tiny", wl, g, 3)
+    assert line["impl"] == "reference" and line["steps"] == 4 and line["warmup"] == 1
+    assert line["value"] > 0 and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]

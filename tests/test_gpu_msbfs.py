@@ -106,7 +106,7 @@ def test_autotune_results_invariant(gb, tmp_path, monkeypatch):
         o = gb.gbf_autotune(g.h, kind)
         assert o.block in (128, 256, 512, 1024)
         assert o.pull_divisor in (10, 14, 20, 28, 40)
-        assert o.heavy_cutoff in (256, 512, 1024, 2048, 4096)
+        assert o.heavy_cutoff in (256, 512, 1024, 2048, 4096, 8192, 16384)
         o2 = gb.gbf_autotune(g.h, kind)          # cached
         assert (o2.block, o2.pull_divisor, o2.heavy_cutoff) == (o.block, o.pull_divisor,
                                                                 o.heavy_cutoff)

@@ -39,13 +39,20 @@ def _bfs_parity(gb, csr, srcs, opts=(None,)):
 
 
 def _wbfs_parity(gb, csr, srcs, opts=(None,)):
+    """Every option set bit-exact against Dijkstra; an option set with the
+    dense switch on must have run at least one dense round on the graph."""
     g = gb.Graph(csr, validate=gb.VALIDATE_BASIC | gb.VALIDATE_SYMMETRIC)
+    dense_rounds = {}
     for s in srcs:
         ref = oracle.dijkstra(csr, int(s))
-        for o in opts:
+        for i, o in enumerate(opts):
             d = g.wbfs(int(s), opt=o)
             assert np.array_equal(d, ref), (csr.name, s, o and (o.bucket_window, o.dense_wbfs))
+            if o is not None and o.dense_wbfs:
+                dense_rounds[i] = dense_rounds.get(i, 0) + g.stats()["pull_rounds"]
     g.close()
+    for i, r in dense_rounds.items():
+        assert r > 0, f"dense_wbfs option set {i} never ran a dense round on {csr.name}"
 
 
 # -------------------------------------------------------------- closed forms
@@ -264,7 +271,7 @@ def test_round_trace(gb):
     assert len(tr) == st["rounds"] and len(tr) >= int(d[d != INF].max())
     assert [r[0] for r in tr] == list(range(1, len(tr) + 1))
     assert all(b[4] >= a[4] for a, b in zip(tr, tr[1:]))
-    assert {r[1] for r in tr} <= {1, 2}
+    assert {r[1] for r in tr} <= {1, 2, 4, 6, 7}
     g.wbfs(s)
     tr = gb.gbf_trace(g.h)
     assert len(tr) == g.stats()["rounds"] > 0
