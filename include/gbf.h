@@ -125,6 +125,7 @@ typedef struct {
   int64_t refills;           /* wBFS: overflow-bucket refills */
   int64_t heavy_vertices;    /* frontier vertices expanded by the blocked edgeMap pass */
   int64_t vertices_pulled;   /* dense rounds: unvisited candidates examined */
+  int64_t device_ns;         /* BFS: %globaltimer time from the kernel's start to its last CTA's end */
   int32_t grid_ctas;         /* CTAs of the persistent launch */
   int32_t block;             /* threads per CTA */
   int32_t device_error;      /* gbf_status reported by the device */
@@ -352,10 +353,11 @@ gbf_status gbf_autotune(gbf_graph *g, int32_t kind, gbf_options *out);
  * device result slot is free (slots are carved once from an HBM budget) and
  * the pending queue has room.  A dispatcher thread keeps engines busy, each
  * with its own stream and workspace: BFS engines coalesce up to max_batch
- * pending BFS queries of one graph into one 64-lane multi-source launch
- * (each lane writes its query's result slot), or run a batch smaller than
- * min_batch as single-source launches; wBFS engines run one weighted query
- * each.  Engines run concurrently on equal shares of the GPU.
+ * pending BFS queries of one graph into one multi-source launch (8-bit lanes
+ * for 2..8 queries, 64-bit lanes above; each lane writes its query's result
+ * slot), or run a batch smaller than min_batch as single-source launches;
+ * wBFS engines run one weighted query each.  Engines run concurrently on
+ * equal shares of the GPU.
  * Results stay on the device until polled.  The paper has no serving layer;
  * results are identical to the single-query calls.
  */
@@ -373,7 +375,7 @@ typedef struct {
   size_t hbm_budget;     /* device bytes for result slots (0 = a quarter of free HBM) */
   gbf_options kernel;    /* kernel knobs (ctas is capped to the engine's share) */
   int32_t min_batch;     /* BFS batches with fewer queries run as single-source launches
-                            (default 8; a 64-lane launch costs about the same at any width) */
+                            (default 2) */
   int32_t reserved;
 } gbf_server_options;
 

@@ -51,7 +51,8 @@ class gbf_stats(ctypes.Structure):
                 ("vertices_expanded", ctypes.c_int64), ("vertices_reached", ctypes.c_int64),
                 ("relaxations", ctypes.c_int64), ("bucket_inserts", ctypes.c_int64),
                 ("refills", ctypes.c_int64), ("heavy_vertices", ctypes.c_int64),
-                ("vertices_pulled", ctypes.c_int64), ("grid_ctas", ctypes.c_int32),
+                ("vertices_pulled", ctypes.c_int64), ("device_ns", ctypes.c_int64),
+                ("grid_ctas", ctypes.c_int32),
                 ("block", ctypes.c_int32), ("device_error", ctypes.c_int32),
                 ("reserved", ctypes.c_int32)]
 

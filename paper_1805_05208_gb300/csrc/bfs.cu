@@ -24,10 +24,10 @@
 //
 // Graph-side arrays used when the graph provides them: a bitmap of the
 // vertices of degree 0 (they start out visited, so no dense level looks at
-// them) and the target of every vertex's first arc (`f1`): the dense step
-// checks that arc from a coalesced stream before it touches the vertex's
-// adjacency list, which is the sequential scan's first step read from a
-// copy.
+// them) and the target of every vertex's first arc (`f1`): when the frontier
+// holds more than an eighth of all arcs, the dense step checks that arc from
+// a coalesced stream before it touches the vertex's adjacency list, which is
+// the sequential scan's first step read from a copy.
 //
 // Readings of Alg. 1 used here: the source is marked visited with D = 0 and
 // vertices first reached while expanding level k-1 get D = k.  A vertex of
@@ -43,7 +43,7 @@
 namespace gbf {
 using namespace dev;
 
-constexpr int kMaxDeferred = 16;  // bitmaps of levels whose D is written at the end
+constexpr int kMaxDeferred = 8;  // bitmaps of levels whose D is written at the end
 
 struct BfsParams {
   DevGraph g;
@@ -131,12 +131,12 @@ struct BfsPushFn {
 // Sparse-direction Update for large frontiers: the winner records its parent
 // and sets its bit of the output bitmap (a reduction, nothing waits for it);
 // D is written directly only when the level has no deferred bitmap.  The
-// winner's offsets are loaded for the next level's frontier size and degree
-// sum and are only used one walk step later, so their round trip overlaps
-// the next step's loads.
+// next frontier's size and degree sum are counted afterwards from the
+// bitmap (count_bitmap), so a winner costs no offset loads here and a walk
+// step keeps kBulkWin windows of loads in flight.
+constexpr int kBulkWin = 8;
 struct BfsBulkPushFn {
-  static constexpr int kWin = kU;
-  const uint32_t *off;
+  static constexpr int kWin = kBulkWin;
   const int32_t *tgt;
   uint32_t *visited;
   uint32_t *fout;
@@ -144,24 +144,9 @@ struct BfsBulkPushFn {
   int32_t *parent;
   int32_t level;
   unsigned long long reached;
-  uint32_t cnt, deg;  // this thread's new vertices of degree >= 2 and their degree sum
-  uint32_t pa[kWin], pz[kWin];
 
-  __device__ __forceinline__ void consume() {
-#pragma unroll
-    for (int r = 0; r < kWin; r++) {
-      const uint32_t d = pz[r] - pa[r];
-      if (d >= 2) {
-        cnt++;
-        deg += d;
-      }
-      pa[r] = pz[r] = 0;
-    }
-  }
   template <class Sink>
-  __device__ __forceinline__ void drain(Sink &, PushSmem &) {
-    consume();
-  }
+  __device__ __forceinline__ void drain(Sink &, PushSmem &) {}
   template <class Sink>
   __device__ __forceinline__ void batch(const bool *val, const int32_t *u, const uint32_t *idx,
                                         Sink &, PushSmem &) {
@@ -171,7 +156,6 @@ struct BfsBulkPushFn {
     for (int r = 0; r < kWin; r++) v[r] = val[r] ? __ldg(tgt + idx[r]) : 0;
 #pragma unroll
     for (int r = 0; r < kWin; r++) wd[r] = val[r] ? visited[v[r] >> 5] : ~0u;
-    consume();  // the previous step's offsets, loaded one step ago
     bool win[kWin];
 #pragma unroll
     for (int r = 0; r < kWin; r++) {
@@ -185,13 +169,56 @@ struct BfsBulkPushFn {
         if (parent) parent[v[r]] = u[r];
         if (dist) dist[v[r]] = level;
         atomicOr(fout + (v[r] >> 5), 1u << (v[r] & 31));  // result unused: a reduction
-        pa[r] = __ldg(off + v[r]);
-        pz[r] = __ldg(off + v[r] + 1);
         reached++;
       }
     }
   }
 };
+
+// Set bits a lane takes per step when it walks its word of a bitmap: their
+// offset loads are in flight together.
+constexpr int kBitBatch = 4;
+
+// Size and degree sum of a frontier bitmap (vertices of degree >= 2), added
+// into *counter with one atomicAdd per CTA: warps take blocks of 32 words,
+// every lane walks the set bits of its word kBitBatch at a time.
+__device__ void count_bitmap(const BfsParams &P, const uint32_t *fb, unsigned long long *counter,
+                             PushSmem &S) {
+  const DevGraph &g = P.g;
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const uint32_t nwords = ((uint32_t)g.n + 31) >> 5;
+  const uint32_t nblk = (nwords + 31) >> 5;
+  const uint32_t gwarp = blockIdx.x * (uint32_t)nw + (threadIdx.x >> 5);
+  const uint32_t twarps = gridDim.x * (uint32_t)nw;
+  uint32_t c = 0, dg = 0;
+  for (uint32_t blk = gwarp; blk < nblk; blk += twarps) {
+    const uint32_t wi = blk * 32 + lane;
+    uint32_t b = wi < nwords ? fb[wi] : 0u;
+    while (b) {  // kBitBatch set bits at a time, their loads in flight together
+      uint32_t a[kBitBatch], z[kBitBatch];
+#pragma unroll
+      for (int k = 0; k < kBitBatch; k++) {
+        a[k] = z[k] = 0u;
+        if (b) {
+          const uint32_t v = wi * 32 + (uint32_t)(__ffs(b) - 1);
+          b &= b - 1;
+          a[k] = __ldg(g.off + v);
+          z[k] = __ldg(g.off + v + 1);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < kBitBatch; k++) {
+        const uint32_t d = z[k] - a[k];
+        if (d >= 2) {
+          c++;
+          dg += d;
+        }
+      }
+    }
+  }
+  const unsigned long long tot = block_sum64(((unsigned long long)c << 32) | dg, S.misc64);
+  if (threadIdx.x == 0 && tot) atomicAdd(counter, tot);
+}
 
 // Sink of the bulk push: nothing is staged; chunk_end keeps the barrier that
 // protects the shared chunk arrays between pieces.
@@ -306,16 +333,15 @@ __device__ __forceinline__ void pull_walk_parked(const BfsParams &P, const uint3
 }
 
 __device__ void pull_level(const BfsParams &P, PushSmem &S, const uint32_t *fin, uint32_t *fout,
-                           bool direct, int32_t level, unsigned long long *counter,
-                           unsigned long long &scanned, unsigned long long &reached,
-                           unsigned long long &pulled, int inv) {
+                           const int32_t *f1, bool direct, int32_t level,
+                           unsigned long long *counter, unsigned long long &scanned,
+                           unsigned long long &reached, unsigned long long &pulled, int inv) {
   const DevGraph &g = P.g;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const uint32_t nwords = ((uint32_t)g.n + 31) >> 5;
   const uint32_t nchunk = (nwords + kChunkWords - 1) / kChunkWords;
   const uint32_t F = (uint32_t)P.pull_serial;
   const unsigned lt = (1u << lane) - 1u;
-  const int32_t *f1 = P.f1;
   const uint32_t skip = f1 ? 1u : 0u;  // arcs already checked before a candidate enters the ring
   int32_t *rv = S.out_v + warp * kRing;
   uint32_t *rs = S.out_d + warp * kRing, *re = S.pref + warp * kRing;
@@ -528,11 +554,14 @@ __device__ bool queue_to_bitmap(const BfsParams &P, const int32_t *q, uint32_t c
 }
 
 // Bitmap -> sparse queue with degree prefix, first-arc offsets and chunk
-// starts, warp by warp over blocks of 32 words (1,024 vertices): a block
-// with no bit set costs one coalesced load; otherwise the warp counts the
-// block's entries (set bits of degree >= 2) and their degrees, reserves its
-// queue and edge range with one 64-bit atomicAdd, and writes the entries.
-// No CTA barrier: warps finish their blocks independently.
+// starts, warp by warp over blocks of 32 words (1,024 vertices), lane l
+// owning word l of the block: a block with no bit set costs one coalesced
+// load; otherwise every lane walks the set bits of its word (all lanes'
+// offset loads in flight together), the warp scans the lanes' entry counts
+// (set bits of degree >= 2) and degree sums, reserves its queue and edge
+// range with one 64-bit atomicAdd, and the lanes walk their bits again to
+// write the entries (the offsets come back from L1/L2).  No CTA barrier:
+// warps finish their blocks independently.
 __device__ void bitmap_to_queue(const BfsParams &P, const uint32_t *fb, const QueueOut &out) {
   const DevGraph &g = P.g;
   const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -540,30 +569,34 @@ __device__ void bitmap_to_queue(const BfsParams &P, const uint32_t *fb, const Qu
   const uint32_t nblk = (nwords + 31) >> 5;
   const uint32_t gwarp = blockIdx.x * (uint32_t)nw + (threadIdx.x >> 5);
   const uint32_t twarps = gridDim.x * (uint32_t)nw;
-  const unsigned lt = lanemask_lt();
   for (uint32_t blk = gwarp; blk < nblk; blk += twarps) {
     const uint32_t wi = blk * 32 + lane;
     const uint32_t bits = wi < nwords ? fb[wi] : 0u;
-    const unsigned nz = __ballot_sync(kFull, bits != 0u);
-    if (nz == 0u) continue;
-    // pass 1: entries and degree sum of every word (lane i keeps word i's)
-    uint32_t wc = 0, wdg = 0;
-    for (unsigned mm = nz; mm; mm &= mm - 1) {
-      const int i = __ffs(mm) - 1;
-      const uint32_t bw = __shfl_sync(kFull, bits, i);
-      const uint32_t v = (blk * 32 + i) * 32 + lane;
-      const bool set = (bw >> lane) & 1u;
-      const uint32_t a = set ? __ldg(g.off + v) : 0u, z = set ? __ldg(g.off + v + 1) : 0u;
-      const bool e = set && z - a >= 2;
-      const uint32_t c = __popc(__ballot_sync(kFull, e));
-      const uint32_t s = __reduce_add_sync(kFull, e ? z - a : 0u);
-      if (lane == i) {
-        wc = c;
-        wdg = s;
+    if (__ballot_sync(kFull, bits != 0u) == 0u) continue;
+    // pass 1: this lane's entries and their degree sum
+    uint32_t c = 0, dg = 0;
+    for (uint32_t b = bits; b;) {
+      uint32_t a[kBitBatch], z[kBitBatch];
+#pragma unroll
+      for (int k = 0; k < kBitBatch; k++) {
+        a[k] = z[k] = 0u;
+        if (b) {
+          const uint32_t v = wi * 32 + (uint32_t)(__ffs(b) - 1);
+          b &= b - 1;
+          a[k] = __ldg(g.off + v);
+          z[k] = __ldg(g.off + v + 1);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < kBitBatch; k++) {
+        const uint32_t d = z[k] - a[k];
+        if (d >= 2) {
+          c++;
+          dg += d;
+        }
       }
     }
-    // exclusive prefix over words; one reservation for the block
-    uint32_t ic = wc, id = wdg;
+    uint32_t ic = c, id = dg;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const uint32_t yc = __shfl_up_sync(kFull, ic, o), yd = __shfl_up_sync(kFull, id, o);
@@ -582,32 +615,31 @@ __device__ void bitmap_to_queue(const BfsParams &P, const uint32_t *fb, const Qu
       if (lane == 0) raise_error(P.ctl, GBF_ERR_OVERFLOW, 12);
       continue;
     }
-    const uint32_t xc = ic - wc, xd = id - wdg;  // exclusive prefixes (lane = word)
-    // pass 2: write the entries (the offsets come back from L1/L2)
-    for (unsigned mm = nz; mm; mm &= mm - 1) {
-      const int i = __ffs(mm) - 1;
-      const uint32_t bw = __shfl_sync(kFull, bits, i);
-      const uint32_t v = (blk * 32 + i) * 32 + lane;
-      const bool set = (bw >> lane) & 1u;
-      const uint32_t a = set ? __ldg(g.off + v) : 0u, z = set ? __ldg(g.off + v + 1) : 0u;
-      const uint32_t d = z - a;
-      const bool e = set && d >= 2;
-      const unsigned eb = __ballot_sync(kFull, e);
-      uint32_t dincl = e ? d : 0u;
+    // pass 2: write this lane's entries at its exclusive prefix
+    uint32_t qi = pos + ic - c, e0 = dpos + id - dg;
+    for (uint32_t b = bits; b;) {
+      uint32_t vv[kBitBatch], a[kBitBatch], z[kBitBatch];
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(kFull, dincl, o);
-        if (lane >= o) dincl += y;
+      for (int k = 0; k < kBitBatch; k++) {
+        vv[k] = a[k] = z[k] = 0u;
+        if (b) {
+          vv[k] = wi * 32 + (uint32_t)(__ffs(b) - 1);
+          b &= b - 1;
+          a[k] = __ldg(g.off + vv[k]);
+          z[k] = __ldg(g.off + vv[k] + 1);
+        }
       }
-      const uint32_t bxc = __shfl_sync(kFull, xc, i), bxd = __shfl_sync(kFull, xd, i);
-      if (e) {
-        const uint32_t qi = pos + bxc + __popc(eb & lt);
-        const uint32_t e0 = dpos + bxd + dincl - d;
-        out.q[qi] = (int32_t)v;
+#pragma unroll
+      for (int k = 0; k < kBitBatch; k++) {
+        const uint32_t d = z[k] - a[k];
+        if (d < 2) continue;
+        out.q[qi] = (int32_t)vv[k];
         out.qoff[qi] = e0;
-        out.adj[qi] = a;
-        for (uint32_t c = (e0 + kFine - 1) >> kFineLog; (c << kFineLog) < e0 + d; c++)
-          if (c < out.cs_cap) out.cs[c] = qi;
+        out.adj[qi] = a[k];
+        for (uint32_t ch = (e0 + kFine - 1) >> kFineLog; (ch << kFineLog) < e0 + d; ch++)
+          if (ch < out.cs_cap) out.cs[ch] = qi;
+        qi++;
+        e0 += d;
       }
     }
   }
@@ -615,36 +647,55 @@ __device__ void bitmap_to_queue(const BfsParams &P, const uint32_t *fb, const Qu
 
 // Distances of the deferred levels, and INF for every vertex never reached,
 // in one coalesced pass; vertices reached in levels that wrote D directly
-// (and the source) keep their value.
+// (and the source) keep their value.  A warp takes blocks of 32 words: lane
+// l loads word l of every bitmap (all loads in flight together), then the
+// warp writes the block's 1,024 distances 128 at a time, each lane 4
+// consecutive vertices with one 16-byte store.
 __device__ void final_dist(const BfsParams &P, int jused, const int32_t *s_lvl) {
   const DevGraph &g = P.g;
-  const uint32_t nwords = ((uint32_t)g.n + 31) >> 5;
-  const uint32_t gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
-  const uint32_t n4 = ((uint32_t)g.n + 3) >> 2;
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const uint32_t n = (uint32_t)g.n;
+  const uint32_t nwords = (n + 31) >> 5;
+  const uint32_t nblk = (nwords + 31) >> 5;
+  const uint32_t gwarp = blockIdx.x * (uint32_t)nw + (threadIdx.x >> 5);
+  const uint32_t twarps = gridDim.x * (uint32_t)nw;
   const bool a16 = ((uintptr_t)P.dist & 15u) == 0;
-  for (uint32_t t = gt; t < n4; t += gs) {
-    const uint32_t v0 = t * 4, w = v0 >> 5, sh = v0 & 31;
-    const uint32_t vis = P.visited[w] & ~(P.iso ? P.iso[w] : 0u);
-    int32_t d[4] = {-2, -2, -2, -2};  // -2: keep
-    for (int j = 0; j < jused; j++) {
-      const uint32_t b = P.lb[(size_t)j * nwords + w] >> sh;
+  for (uint32_t blk = gwarp; blk < nblk; blk += twarps) {
+    const uint32_t wi = blk * 32 + lane;
+    const bool in = wi < nwords;
+    // reached in a direct level (or the source): keep
+    uint32_t keep = in ? P.visited[wi] & ~(P.iso ? P.iso[wi] : 0u) : 0u;
+    if (in && wi == ((uint32_t)P.src >> 5)) keep |= 1u << (P.src & 31);
+    uint32_t lw[kMaxDeferred];
 #pragma unroll
-      for (int k = 0; k < 4; k++)
-        if ((b >> k) & 1u) d[k] = s_lvl[j];
-    }
-    bool all = true;
+    for (int j = 0; j < kMaxDeferred; j++)
+      lw[j] = (j < jused && in) ? P.lb[(size_t)j * nwords + wi] : 0u;
 #pragma unroll
-    for (int k = 0; k < 4; k++) {
-      const uint32_t v = v0 + k;
-      if (d[k] == -2 && v != (uint32_t)P.src && !((vis >> (sh + k)) & 1u)) d[k] = kInf;
-      if (d[k] == -2 || v >= (uint32_t)g.n) all = false;
-    }
-    if (all && a16 && v0 + 3 < (uint32_t)g.n) {
-      *reinterpret_cast<int4 *>(P.dist + v0) = make_int4(d[0], d[1], d[2], d[3]);
-    } else {
+    for (int j = 0; j < kMaxDeferred; j++) keep &= ~lw[j];
+    // step q: vertices blk*1024 + 128 q + 4 lane .. + 3, in word 4 q + lane / 8
+    for (int q = 0; q < 8; q++) {
+      const int sl = 4 * q + (lane >> 3);
+      const uint32_t sh = 4u * (uint32_t)(lane & 7);
+      const uint32_t kp = __shfl_sync(kFull, keep, sl) >> sh;
+      int32_t d[4] = {kInf, kInf, kInf, kInf};
 #pragma unroll
-      for (int k = 0; k < 4; k++)
-        if (d[k] != -2 && v0 + k < (uint32_t)g.n) P.dist[v0 + k] = d[k];
+      for (int j = 0; j < kMaxDeferred; j++) {
+        if (j < jused) {
+          const uint32_t b = __shfl_sync(kFull, lw[j], sl) >> sh;
+          const int32_t lv = s_lvl[j];
+#pragma unroll
+          for (int k = 0; k < 4; k++)
+            if ((b >> k) & 1u) d[k] = lv;
+        }
+      }
+      const uint32_t v0 = blk * 1024u + 128u * (uint32_t)q + 4u * (uint32_t)lane;
+      if (a16 && (kp & 15u) == 0 && v0 + 4 <= n) {
+        *reinterpret_cast<int4 *>(P.dist + v0) = make_int4(d[0], d[1], d[2], d[3]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+          if (v0 + k < n && !((kp >> k) & 1u)) P.dist[v0 + k] = d[k];
+      }
     }
   }
 }
@@ -715,12 +766,14 @@ __global__ void __launch_bounds__(1024) bfs_kernel(BfsParams P) {
         (unsigned long long)cnt * (unsigned)P.pull_stay > (unsigned long long)g.n)
       dense = true;
     bool converted = false;
+    long long t_mid = 0;  // end of the level's first phase (conversion, or push before its count)
     // the input frontier in the form this direction reads
     if (!dense && in_bm) {
       unsigned long long *cv = &ctl->cv[level % 3];
       QueueOut out{P.q[0], P.qoff[0], P.qadj[0], P.cs[0], cv, (uint32_t)g.n, P.cs_cap};
       bitmap_to_queue(P, fin, out);
       if (!grid_sync(ctl, bar, &s_flag)) break;
+      t_mid = (long long)(globaltimer() - t_start);
       const unsigned long long c2 = ld_vol(*cv);
       cnt = (uint32_t)(c2 >> 32);
       D = (uint32_t)c2;
@@ -788,19 +841,21 @@ __global__ void __launch_bounds__(1024) bfs_kernel(BfsParams P) {
         reached += fn.reached;
         qb ^= 1;
       } else {
-        BfsBulkPushFn fn{g.off, g.tgt, P.visited, fout, direct ? P.dist : nullptr, P.parent,
-                         level, 0, 0u, 0u, {0u, 0u, 0u, 0u}, {0u, 0u, 0u, 0u}};
+        BfsBulkPushFn fn{g.tgt, P.visited, fout, direct ? P.dist : nullptr, P.parent, level, 0};
         NullSink sink;
         // nothing is staged, so a chunk may span many walk steps
         const int s = chunk_shift(D, 4u, 6);
         blocked_edge_map(g, in, s, (uint32_t)P.bmax, S, fn, sink, ctl, bem++);
         reached += fn.reached;
-        const unsigned long long packed = ((unsigned long long)fn.cnt << 32) | fn.deg;
-        const unsigned long long tot = block_sum64(packed, S.misc64);
-        if (threadIdx.x == 0 && tot) atomicAdd(outc, tot);
+        if (!grid_sync(ctl, bar, &s_flag)) break;
+        t_mid = (long long)(globaltimer() - t_start);
+        count_bitmap(P, fout, outc, S);
       }
     } else {
-      pull_level(P, S, fin, fout, direct, level, outc, scanned, reached, pulled, bem++);
+      // the first-arc check pays when a random arc leads into the frontier
+      // often: its chance is about the frontier's share of all arcs
+      const int32_t *f1 = (unsigned long long)D * 8ull > g.m ? P.f1 : nullptr;
+      pull_level(P, S, fin, fout, f1, direct, level, outc, scanned, reached, pulled, bem++);
     }
     if (!grid_sync(ctl, bar, &s_flag)) break;
     fr = ld_vol(*outc);
@@ -817,7 +872,8 @@ __global__ void __launch_bounds__(1024) bfs_kernel(BfsParams P) {
       // 6 -> 7) after a bitmap -> queue conversion
       int kind = dense ? 2 : bulk ? 6 : 1;
       if (converted) kind = kind == 1 ? 4 : 7;
-      P.trace[level - 1] = TraceRec{level, kind, cnt, D, (long long)(globaltimer() - t_start), 0};
+      P.trace[level - 1] =
+          TraceRec{level, kind, cnt, D, (long long)(globaltimer() - t_start), t_mid};
     }
     level++;
   }
@@ -825,6 +881,10 @@ __global__ void __launch_bounds__(1024) bfs_kernel(BfsParams P) {
     __syncthreads();
     if (ld_vol(ctl->err) == 0) final_dist(P, jn, s_lvl);
   }
+  // the last CTA to get here records the kernel's end (for the trace)
+  __syncthreads();
+  if (threadIdx.x == 0 && atomicAdd(&ctl->done, 1u) == gridDim.x - 1)
+    st_vol(ctl->t_end_ns, (long long)(globaltimer() - t_start));
   // statistics
   unsigned long long t;
   t = block_sum64(scanned, S.misc64);
@@ -835,6 +895,12 @@ __global__ void __launch_bounds__(1024) bfs_kernel(BfsParams P) {
   if (threadIdx.x == 0 && t) atomicAdd(&ctl->expanded, t);
   t = block_sum64(pulled, S.misc64);
   if (threadIdx.x == 0 && t) atomicAdd(&ctl->pulled, t);
+}
+
+// Dynamic shared memory of bfs_kernel for a heavy cutoff and block size (the
+// dense step's rings live inside the staging area).
+static size_t bfs_smem_bytes(int heavy_cutoff, int block) {
+  return push_smem_bytes(SmemShape{heavy_cutoff, stage_capacity(block), 0, 0, 1});
 }
 
 gbf_status launch_bfs(Graph &g, Workspace &ws, int32_t src, int32_t *dist, int32_t *parent,
@@ -868,7 +934,7 @@ gbf_status launch_bfs(Graph &g, Workspace &ws, int32_t src, int32_t *dist, int32
   P.pull_serial = o.pull_serial;
   P.inject_wait = o.inject_wait;
   P.cap_ns = o.spin_cap_ns;
-  const size_t smem = push_smem_bytes(SmemShape{P.bmax, P.cap, 0, 0, 1});
+  const size_t smem = bfs_smem_bytes(o.heavy_cutoff, o.block);
   {
     const gbf_status sm = check_smem(smem, "bfs_kernel");
     if (sm != GBF_OK) return sm;
@@ -895,7 +961,7 @@ gbf_status launch_bfs(Graph &g, Workspace &ws, int32_t src, int32_t *dist, int32
 }
 
 int resident_ctas_per_sm_bfs(const Opts &o) {
-  const size_t smem = push_smem_bytes(SmemShape{o.heavy_cutoff, stage_capacity(o.block), 0, 0, 1});
+  const size_t smem = bfs_smem_bytes(o.heavy_cutoff, o.block);
   if (cudaFuncSetAttribute(bfs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return 0;

@@ -30,6 +30,8 @@ struct Ctl {
   int err;                     // gbf_status raised on the device (0 = ok)
   int err_where;               // where it was raised (debug)
   int stop;                    // fault injection flag nobody sets
+  unsigned int done;           // CTAs past their last phase (BFS end-of-kernel time stamp)
+  long long t_end_ns;          // BFS: %globaltimer time of the last CTA's end, since its start
   unsigned long long fr[3];    // frontier counters (count << 32 | degree sum), by round % 3
   unsigned long long conv;     // conversion cursor (same packing)
   unsigned long long cv[3];    // BFS bitmap -> queue conversions (same packing), by level % 3
@@ -111,7 +113,7 @@ struct Workspace {
   cudaStream_t ms_stream = nullptr;
   cudaEvent_t ms_ready = nullptr, ms_done = nullptr;
   cudaGraphExec_t ms_exec = nullptr;
-  long long ms_key[6] = {0, 0, 0, 0, 0, 0};
+  long long ms_key[7] = {0, 0, 0, 0, 0, 0, 0};
   int ms_grid = 0;
   // betweenness (lazy): path counts / coefficients, levels, chunk starts of
   // every level, per-level descriptors, fp64 output staging for host buffers

@@ -369,6 +369,7 @@ gbf_status ws_collect(Workspace &ws, cudaStream_t st, gbf_stats *stats) {
     stats->refills = c.refills;
     stats->heavy_vertices = (int64_t)c.heavy;
     stats->vertices_pulled = (int64_t)c.pulled;
+    stats->device_ns = c.t_end_ns;
     stats->grid_ctas = ws.last_grid;
     stats->block = ws.last_block;
     stats->device_error = c.err;

@@ -22,7 +22,14 @@
 // The graph, sources, k and the output rows are read from a device parameter
 // block (MsCall), so one captured CUDA graph replays any call on any graph
 // the workspace is sized for.
+//
+// Lane words come in two widths: 64-bit lanes for batches of more than 8
+// sources, and 8-bit lanes (one byte per vertex, four vertices per 32-bit
+// word for the atomic ORs) for batches of 2..8, whose per-vertex arrays are
+// an eighth of the size and stay in L2 at the serving graphs' sizes.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "dev_common.cuh"
 #include "gbf_impl.h"
@@ -40,9 +47,9 @@ struct MsCall {
 
 struct MsParams {
   const MsCall *call;
-  unsigned long long *seen;
-  unsigned long long *visit[2];
-  unsigned long long *next;
+  void *seen;       // lane words (LaneT of the kernel instance), n each
+  void *visit[2];
+  void *next;
   int32_t *q[3];
   uint32_t *qoff[3];
   uint32_t *qadj[3];
@@ -63,6 +70,34 @@ struct MsParams {
 namespace {
 
 typedef unsigned long long u64;
+
+// Access to the per-vertex lane words of one width; values travel as u64.
+template <class T>
+struct Lanes;
+template <>
+struct Lanes<u64> {
+  static __device__ __forceinline__ u64 ld(const void *a, uint32_t v) { return ((const u64 *)a)[v]; }
+  static __device__ __forceinline__ void st(void *a, uint32_t v, u64 x) { ((u64 *)a)[v] = x; }
+  // atomic OR of m into vertex v's word; returns the word before
+  static __device__ __forceinline__ u64 bor(void *a, uint32_t v, u64 m) {
+    return atomicOr((u64 *)a + v, m);
+  }
+};
+template <>
+struct Lanes<uint8_t> {
+  static __device__ __forceinline__ u64 ld(const void *a, uint32_t v) {
+    return (u64)((const uint8_t *)a)[v];
+  }
+  static __device__ __forceinline__ void st(void *a, uint32_t v, u64 x) {
+    ((uint8_t *)a)[v] = (uint8_t)x;
+  }
+  // the byte of v inside its aligned 32-bit word (the array is 4-byte aligned)
+  static __device__ __forceinline__ u64 bor(void *a, uint32_t v, u64 m) {
+    unsigned *w = (unsigned *)((uint8_t *)a + (v & ~3u));
+    const unsigned sh = 8u * (v & 3u);
+    return (u64)((atomicOr(w, (unsigned)m << sh) >> sh) & 0xffu);
+  }
+};
 
 // Warp-collective: write level L into dist[i][v] for every lane bit i of
 // `bits`, iterating lanes so that a warp of consecutive v writes each row
@@ -118,14 +153,15 @@ struct TouchSink {
 };
 
 // Push Update for kU windows: lanes visit[u] & ~seen[v] are OR-ed into next[v].
+template <class T>
 struct MsPushFn {
   static constexpr int kWin = kU;  // windows per walk step
   template <class Sink>
   __device__ __forceinline__ void drain(Sink &, PushSmem &) {}  // nothing deferred
   const int32_t *tgt;
-  const u64 *cur;
-  const u64 *seen;
-  u64 *next;
+  const void *cur;
+  const void *seen;
+  void *next;
   unsigned long long scanned;
   template <class Sink>
   __device__ __forceinline__ void batch(const bool *val, const int32_t *u, const uint32_t *idx,
@@ -135,16 +171,16 @@ struct MsPushFn {
 #pragma unroll
     for (int r = 0; r < kU; r++) {
       v[r] = val[r] ? __ldg(tgt + idx[r]) : 0;
-      w[r] = val[r] ? cur[u[r]] : 0ull;
+      w[r] = val[r] ? Lanes<T>::ld(cur, (uint32_t)u[r]) : 0ull;
     }
 #pragma unroll
-    for (int r = 0; r < kU; r++) sv[r] = val[r] ? seen[v[r]] : ~0ull;
+    for (int r = 0; r < kU; r++) sv[r] = val[r] ? Lanes<T>::ld(seen, (uint32_t)v[r]) : ~0ull;
     bool first[kU];
 #pragma unroll
     for (int r = 0; r < kU; r++) {
       const u64 m = w[r] & ~sv[r];
       first[r] = false;
-      if (m) first[r] = atomicOr(next + v[r], m) == 0ull;
+      if (m) first[r] = Lanes<T>::bor(next, (uint32_t)v[r], m) == 0ull;
     }
     sink.template append_n<kU>(S, first, v, nullptr, nullptr);
   }
@@ -152,7 +188,9 @@ struct MsPushFn {
 
 }  // namespace
 
+template <class T>
 __global__ void __launch_bounds__(1024) msbfs_kernel(MsParams P) {
+  typedef Lanes<T> LN;
   extern __shared__ unsigned long long smem_raw[];
   __shared__ int s_flag;
   PushSmem S = carve_push_smem(smem_raw, SmemShape{P.bmax, P.cap, 0, 0, 1});
@@ -170,10 +208,10 @@ __global__ void __launch_bounds__(1024) msbfs_kernel(MsParams P) {
   const unsigned long long t_start = globaltimer();
 
   for (uint32_t i = gt; i < n; i += gs) {
-    P.seen[i] = 0ull;
-    P.visit[0][i] = 0ull;
-    P.visit[1][i] = 0ull;
-    P.next[i] = 0ull;
+    LN::st(P.seen, i, 0ull);
+    LN::st(P.visit[0], i, 0ull);
+    LN::st(P.visit[1], i, 0ull);
+    LN::st(P.next, i, 0ull);
   }
   if (P.inject_wait && blockIdx.x == 0 && threadIdx.x == 0) injected_wait(ctl, P.cap_ns);
   bool ok = grid_sync(ctl, bar, &s_flag);
@@ -185,8 +223,8 @@ __global__ void __launch_bounds__(1024) msbfs_kernel(MsParams P) {
     uint32_t d = 0, a = 0;
     if ((int)threadIdx.x < k) {
       s = P.call->srcs[threadIdx.x];
-      atomicOr(P.seen + s, 1ull << threadIdx.x);
-      atomicOr(P.visit[0] + s, 1ull << threadIdx.x);
+      LN::bor(P.seen, (uint32_t)s, 1ull << threadIdx.x);
+      LN::bor(P.visit[0], (uint32_t)s, 1ull << threadIdx.x);
       rows[threadIdx.x][s] = 0;
       bool dup = false;
       for (int j = 0; j < (int)threadIdx.x; j++) dup |= P.call->srcs[j] == s;
@@ -206,8 +244,8 @@ __global__ void __launch_bounds__(1024) msbfs_kernel(MsParams P) {
     const uint32_t cnt = (uint32_t)(fr >> 32), D = (uint32_t)fr;
     if (cnt == 0) break;
     const int qc = (L - 1) % 3, qn = L % 3, qo = (L + 1) % 3;  // queues of levels L-1, L, L-2
-    const u64 *cur = P.visit[(L - 1) & 1];
-    u64 *nxt = P.visit[L & 1];
+    const void *cur = P.visit[(L - 1) & 1];
+    void *nxt = P.visit[L & 1];
     const bool dense =
         P.pull_divisor > 0 && (unsigned long long)D * (unsigned)P.pull_divisor > g.m;
     unsigned long long *outc = &ctl->fr[qn];
@@ -224,11 +262,12 @@ __global__ void __launch_bounds__(1024) msbfs_kernel(MsParams P) {
       // source when L == 2): clear it while the push reads cur
       if (L >= 2) {
         const uint32_t c2 = (uint32_t)(ld_vol(ctl->fr[qo]) >> 32);
-        for (uint32_t i = gt; i < c2; i += gs) nxt[P.q[qo][i]] = 0ull;
-        if (L == 2 && blockIdx.x == 0 && (int)threadIdx.x < k) nxt[P.call->srcs[threadIdx.x]] = 0ull;
+        for (uint32_t i = gt; i < c2; i += gs) LN::st(nxt, (uint32_t)P.q[qo][i], 0ull);
+        if (L == 2 && blockIdx.x == 0 && (int)threadIdx.x < k)
+          LN::st(nxt, (uint32_t)P.call->srcs[threadIdx.x], 0ull);
       }
       QueueIn in{P.q[qc], P.qoff[qc], P.qadj[qc], P.cs[qc], cnt, D};
-      MsPushFn fn{g.tgt, cur, P.seen, P.next, 0};
+      MsPushFn<T> fn{g.tgt, cur, P.seen, P.next, 0};
       TouchSink sink{P.touched, tcount, n, ctl};
       blocked_edge_map(g, in, chunk_shift(D, 4u, 8), (uint32_t)P.bmax, S, fn, sink,
                        ctl, bem++);
@@ -247,12 +286,13 @@ __global__ void __launch_bounds__(1024) msbfs_kernel(MsParams P) {
         uint32_t d = 0, a = 0;
         if (i < tc) {
           v = P.touched[i];
-          const u64 x = P.next[v];
-          P.next[v] = 0ull;
-          nwb = x & ~P.seen[v];
+          const u64 x = LN::ld(P.next, (uint32_t)v);
+          LN::st(P.next, (uint32_t)v, 0ull);
+          const u64 sv = LN::ld(P.seen, (uint32_t)v);
+          nwb = x & ~sv;
           if (nwb) {
-            P.seen[v] |= nwb;
-            nxt[v] = nwb;
+            LN::st(P.seen, (uint32_t)v, sv | nwb);
+            LN::st(nxt, (uint32_t)v, nwb);
             a = __ldg(g.off + v);
             d = __ldg(g.off + v + 1) - a;
             reached += __popcll(nwb);
@@ -281,7 +321,7 @@ __global__ void __launch_bounds__(1024) msbfs_kernel(MsParams P) {
         const uint32_t wi = base + warp;
         const int32_t v = (int32_t)(wi * 32 + lane);
         const bool inr = wi < whi && (uint32_t)v < n;
-        const u64 sv = inr ? P.seen[v] : ALL;
+        const u64 sv = inr ? LN::ld(P.seen, (uint32_t)v) : ALL;
         uint32_t s = 0, e = 0;
         bool cand = inr && sv != ALL;
         if (cand) {
@@ -293,7 +333,7 @@ __global__ void __launch_bounds__(1024) msbfs_kernel(MsParams P) {
         uint32_t kk = s;
         if (cand) {
           const uint32_t lim = min(e, s + (uint32_t)P.pull_serial);
-          for (; kk < lim && ((acc | sv) != ALL); kk++) acc |= cur[__ldg(g.tgt + kk)];
+          for (; kk < lim && ((acc | sv) != ALL); kk++) acc |= LN::ld(cur, (uint32_t)__ldg(g.tgt + kk));
           scanned += kk - s;
         }
         unsigned rm = __ballot_sync(kFull, cand && ((acc | sv) != ALL) && kk < e);
@@ -306,7 +346,7 @@ __global__ void __launch_bounds__(1024) msbfs_kernel(MsParams P) {
           uint32_t looked = 0;
           for (uint32_t c0 = ks; c0 < ke && ((wacc & need) != need); c0 += 32) {
             const uint32_t c = c0 + lane;
-            const u64 x = (c < ke) ? cur[__ldg(g.tgt + c)] : 0ull;
+            const u64 x = (c < ke) ? LN::ld(cur, (uint32_t)__ldg(g.tgt + c)) : 0ull;
             const unsigned xl = __reduce_or_sync(kFull, (unsigned)x);
             const unsigned xh = __reduce_or_sync(kFull, (unsigned)(x >> 32));
             wacc |= ((u64)xh << 32) | xl;
@@ -319,9 +359,9 @@ __global__ void __launch_bounds__(1024) msbfs_kernel(MsParams P) {
         }
         const u64 nwb = acc & ~sv & ALL;
         if (inr) {
-          nxt[v] = nwb;
+          LN::st(nxt, (uint32_t)v, nwb);
           if (nwb) {
-            P.seen[v] = sv | nwb;
+            LN::st(P.seen, (uint32_t)v, sv | nwb);
             reached += __popcll(nwb);
           }
         }
@@ -344,7 +384,7 @@ __global__ void __launch_bounds__(1024) msbfs_kernel(MsParams P) {
     const uint32_t gw = gt >> 5, tw = gs >> 5;
     for (uint32_t wi = gw; wi < nwords; wi += tw) {
       const uint32_t v = wi * 32 + lane;
-      const u64 miss = (v < n) ? (ALL & ~P.seen[v]) : 0ull;
+      const u64 miss = (v < n) ? (ALL & ~LN::ld(P.seen, v)) : 0ull;
       write_rows(rows, k, (int32_t)v, miss, kInf);
     }
   }
@@ -374,10 +414,11 @@ gbf_status launch_msbfs_rows(Graph &g, Workspace &ws, const int32_t *srcs_host, 
   }
   hc->k = k;
   hc->pad = 0;
-  const long long key[6] = {o.block, o.pull_divisor, o.heavy_cutoff, o.pull_serial, o.ctas,
-                            o.spin_cap_ns};
+  const bool narrow = k <= 8;  // 8-bit lanes
+  const long long key[7] = {o.block, o.pull_divisor, o.heavy_cutoff, o.pull_serial, o.ctas,
+                            o.spin_cap_ns, narrow ? 1 : 0};
   bool same = ws.ms_exec != nullptr;
-  for (int i = 0; i < 6 && same; i++) same = ws.ms_key[i] == key[i];
+  for (int i = 0; i < 7 && same; i++) same = ws.ms_key[i] == key[i];
   same = same && o.inject_wait == 0;
   if (!same) {
     if (ws.ms_exec) {
@@ -389,6 +430,7 @@ gbf_status launch_msbfs_rows(Graph &g, Workspace &ws, const int32_t *srcs_host, 
     P.seen = ws.ms_seen;
     P.visit[0] = ws.ms_visit;
     P.visit[1] = ws.ms_visit + (size_t)ws.n;  // the workspace's size, not this graph's
+    const void *kern = narrow ? (const void *)msbfs_kernel<uint8_t> : (const void *)msbfs_kernel<u64>;
     P.next = ws.ms_next;
     for (int i = 0; i < 3; i++) {
       P.q[i] = ws.ms_q[i];
@@ -412,10 +454,9 @@ gbf_status launch_msbfs_rows(Graph &g, Workspace &ws, const int32_t *srcs_host, 
     const gbf_status sm = check_smem(smem, "msbfs_kernel");
     if (sm != GBF_OK) return sm;
   }
-  GBF_CUDA(cudaFuncSetAttribute(msbfs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem));
+    GBF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    GBF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, msbfs_kernel, o.block, smem));
+    GBF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, o.block, smem));
     if (per_sm < 1) {
       set_error("msbfs kernel does not fit on an SM with this block size");
       return GBF_ERR_INVALID;
@@ -429,8 +470,7 @@ gbf_status launch_msbfs_rows(Graph &g, Workspace &ws, const int32_t *srcs_host, 
     cudaMemsetAsync(ws.ctl, 0, sizeof(Ctl), cs);
     cudaMemsetAsync(ws.trace, 0, sizeof(TraceRec) * (size_t)ws.trace_cap, cs);
     void *args[] = {&P};
-    cudaError_t le = cudaLaunchCooperativeKernel((const void *)msbfs_kernel, dim3(grid),
-                                                 dim3(o.block), args, smem, cs);
+    cudaError_t le = cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(o.block), args, smem, cs);
     cudaGraph_t graph = nullptr;
     cudaError_t ce = cudaStreamEndCapture(cs, &graph);
     if (le != cudaSuccess) {
@@ -444,7 +484,7 @@ gbf_status launch_msbfs_rows(Graph &g, Workspace &ws, const int32_t *srcs_host, 
       ws.ms_exec = nullptr;
       return cuda_fail(ie, "cudaGraphInstantiate");
     }
-    for (int i = 0; i < 6; i++) ws.ms_key[i] = o.inject_wait ? -1 : key[i];
+    for (int i = 0; i < 7; i++) ws.ms_key[i] = o.inject_wait ? -1 : key[i];
   }
   // order: user stream -> graph replay on the workspace stream -> user stream
   GBF_CUDA(cudaEventRecord(ws.ms_ready, user_st));
@@ -467,13 +507,18 @@ gbf_status launch_msbfs(Graph &g, Workspace &ws, const int32_t *srcs_host, int32
 
 int resident_ctas_per_sm_msbfs(const Opts &o) {
   const size_t smem = push_smem_bytes(SmemShape{o.heavy_cutoff, stage_capacity(o.block), 0, 0, 1});
-  if (cudaFuncSetAttribute(msbfs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-      cudaSuccess)
-    return 0;
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, msbfs_kernel, o.block, smem) != cudaSuccess)
-    return 0;
-  return per_sm;
+  int best = 0;
+  for (int w = 0; w < 2; w++) {  // the fewer of the two widths
+    const void *kern = w ? (const void *)msbfs_kernel<uint8_t> : (const void *)msbfs_kernel<u64>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+      return 0;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, o.block, smem) != cudaSuccess)
+      return 0;
+    best = w == 0 ? per_sm : std::min(best, per_sm);
+  }
+  return best;
 }
 
 }  // namespace gbf

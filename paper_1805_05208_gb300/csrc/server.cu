@@ -6,12 +6,11 @@
 // returns GBF_ERR_BUSY.  A dispatcher thread keeps a set of engines busy,
 // each with its own CUDA stream and workspace:
 //   - BFS engines take up to max_batch pending BFS requests of one graph
-//     (the graph whose oldest request is oldest) and run them as one 64-lane
-//     multi-source BFS launch whose lane i writes straight into request i's
-//     result slot.  A 64-lane launch costs about the same whatever the
-//     number of lanes in use, so a batch smaller than min_batch runs as
-//     single-source BFS launches back to back instead (and max_batch = 1
-//     gives one query per launch);
+//     (the graph whose oldest request is oldest) and run them as one
+//     multi-source BFS launch (8-bit lanes for 2..8 requests, 64-bit lanes
+//     above) whose lane i writes straight into request i's result slot; a
+//     batch smaller than min_batch runs as single-source BFS launches back to
+//     back instead (and max_batch = 1 gives one query per launch);
 //   - wBFS engines take the oldest weighted request.
 // Engines run concurrently; each persistent launch gets an equal share of
 // the GPU's resident CTAs, so all engines' CTAs can be co-resident at once.
@@ -240,7 +239,7 @@ gbf_status gbf_server_options_default(gbf_server_options *o) {
   o->bfs_engines = 2;
   o->wbfs_engines = 2;
   o->max_batch = 64;
-  o->min_batch = 8;
+  o->min_batch = 2;
   o->max_queue = 1 << 16;
   o->hbm_budget = 0;
   gbf_options_default(&o->kernel);

@@ -1,7 +1,8 @@
-"""GPU parity for the 64-lane multi-source BFS: lane i must equal a BFS from
-srcs[i] (the oracle's, bit-exact), for every lane, on seeded graphs, with
-duplicate and isolated sources, both directions of edgeMap, and CUDA-graph
-replays with new sources and new output buffers."""
+"""GPU parity for the multi-source BFS (64-bit lanes, and 8-bit lanes for 2..8
+sources): lane i must equal a BFS from srcs[i] (the oracle's, bit-exact), for
+every lane, on seeded graphs, with duplicate and isolated sources, both
+directions of edgeMap, and CUDA-graph replays with new sources, new output
+buffers and alternating lane widths."""
 import numpy as np
 import pytest
 
@@ -50,6 +51,33 @@ def test_msbfs_k_sizes_duplicates_isolated(gb):
         s[5] = int(iso[0])           # an isolated source
     for k in (1, 2, 31, 32, 33, 40):
         _check(gb, csr, np.array(s[:k], dtype=np.int32))
+
+
+@pytest.mark.parametrize("scale", [12, 16])
+def test_msbfs_narrow_lanes(gb, scale):
+    """2..8 sources run with 8-bit lanes (four vertices per atomic word); 9 is
+    the first batch with 64-bit lanes."""
+    csr = G.rmat(scale, 16, seed=50 + scale)
+    s = list(G.sources(csr, 9, seed=51))
+    s[2] = s[1]                      # duplicate lane
+    opts = (None, gb.gbf_options_default(pull_divisor=-1),
+            gb.gbf_options_default(pull_divisor=1000),
+            gb.gbf_options_default(block=128, heavy_cutoff=256, ctas=7))
+    for k in (2, 3, 4, 7, 8, 9):
+        _check(gb, csr, np.array(s[:k], dtype=np.int32), opts=opts)
+
+
+def test_msbfs_replay_alternating_widths(gb):
+    import torch
+    csr = G.rmat(13, 16, seed=12)
+    g = gb.Graph(csr)
+    for rep, k in enumerate((4, 64, 4, 8, 64, 2)):
+        srcs = G.sources(csr, k, seed=200 + rep)
+        out = torch.full((k, csr.n), -5, dtype=torch.int32, device="cuda")
+        gb.gbf_msbfs(g.h, srcs, out)
+        assert gb.gbf_wait(g.h)["device_error"] == 0
+        assert np.array_equal(out.cpu().numpy(), oracle.msbfs(csr, srcs)), (rep, k)
+    g.close()
 
 
 def test_msbfs_grid_and_paths(gb):

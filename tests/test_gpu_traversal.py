@@ -120,6 +120,12 @@ def test_bfs_repeated_block1024_conversions(gb):
             for s in srcs:
                 d, _ = g.bfs(int(s), opt=opt)
                 assert np.array_equal(d, refs[int(s)]), (blk, hc, int(s))
+    # a shape whose shared memory does not fit one CTA is refused, not run
+    with pytest.raises(gb.GbfError) as e:
+        g.bfs(int(srcs[0]), opt=gb.gbf_options_default(block=1024, heavy_cutoff=16384))
+    assert e.value.status == 1
+    d, _ = g.bfs(int(srcs[0]))
+    assert np.array_equal(d, refs[int(srcs[0])])
     g.close()
 
 
