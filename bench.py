@@ -647,21 +647,26 @@ def run_serve(args, wl, rank, world):
     hs = [gb.Graph(c, validate=gb.VALIDATE_BASIC) for c in csrs]
     rates = [int(r) for r in (args.rates.split(",") if args.rates else wl["rates"])]
     warm, meas = (args.serve_warm or wl["warm"]), (args.serve_meas or wl["meas"])
+    # each mode at every weighted-engine share of the GPU (0 = equal shares
+    # per engine); each mode is credited with its best share
+    shares = [int(x) for x in args.serve_shares.split(",")]
     modes = {
-        "batched": gb.gbf_server_options_default(bfs_engines=args.serve_engines[0],
-                                                 wbfs_engines=args.serve_engines[1], max_batch=64),
-        "one_per_launch_fifo": gb.gbf_server_options_default(bfs_engines=1, wbfs_engines=1,
-                                                             max_batch=1),
+        "batched": dict(bfs_engines=args.serve_engines[0], wbfs_engines=args.serve_engines[1],
+                        max_batch=64),
+        "one_per_launch_fifo": dict(bfs_engines=1, wbfs_engines=1, max_batch=1),
     }
     res = {}
     with ClockSampler(0) as clk:
-        for name, opt in modes.items():
+        for name, kw in modes.items():
             res[name] = []
-            for r in rates:
-                thr, p50, p99, st = serve_run(gb, hs, csrs, opt, r, warm, meas, seed=4)
-                res[name].append({"offered_qps": r, "qps": thr, "p50_us": p50, "p99_us": p99,
-                                  "mean_batch": st["batched_queries"] / max(1, st["batches"]),
-                                  "failed": st["failed"]})
+            for sh in shares:
+                opt = gb.gbf_server_options_default(wbfs_share=sh, **kw)
+                for r in rates:
+                    thr, p50, p99, st = serve_run(gb, hs, csrs, opt, r, warm, meas, seed=4)
+                    res[name].append({"offered_qps": r, "wbfs_share": sh, "qps": thr,
+                                      "p50_us": p50, "p99_us": p99,
+                                      "mean_batch": st["batched_queries"] / max(1, st["batches"]),
+                                      "failed": st["failed"]})
     best = max(x["qps"] for x in res["batched"])
     base = max(x["qps"] for x in res["one_per_launch_fifo"])
     clocks = clk.summary()
@@ -845,8 +850,10 @@ def main():
     ap.add_argument("--rates", default="", help="serve: comma list of offered rates (q/s)")
     ap.add_argument("--serve-warm", type=int, default=0)
     ap.add_argument("--serve-meas", type=int, default=0)
-    ap.add_argument("--serve-engines", default="2,2",
+    ap.add_argument("--serve-engines", default="1,1",
                     help="serve: BFS,wBFS engines of the batched server")
+    ap.add_argument("--serve-shares", default="67",
+                    help="serve: comma list of weighted-engine GPU shares (percent; 0 = equal)")
     args = ap.parse_args()
     args.serve_engines = tuple(int(x) for x in args.serve_engines.split(","))
     args.warmup = max(args.warmup, 3)

@@ -329,6 +329,21 @@ gbf_status gbf_wait(gbf_graph *g, void *cuda_stream, gbf_stats *stats);
 gbf_status gbf_msbfs(gbf_graph *g, const int32_t *srcs, int32_t k, int32_t *dist, int mem,
                      const gbf_options *opt, void *cuda_stream);
 
+/*
+ * gbf_mssp — shortest-path distances (§4 "Integral-Weight SSSP") from k
+ * sources (1 <= k <= 8) on a weighted graph in one persistent launch: the
+ * frontier rounds of Bellman-Ford (Alg. 4) with one int32 distance lane per
+ * source, the 8 lanes of a vertex stored together so that every arc read and
+ * every round serves all sources.  The distances equal gbf_wbfs's.
+ *   srcs  int32[k] in host memory (duplicates allowed)
+ *   dist  int32[k*n], row i = distances from srcs[i] (GBF_INF if unreachable)
+ *   mem   where dist lives; GBF_HOST blocks, GBF_DEVICE is stream-ordered
+ * Errors: GBF_ERR_INVALID for an unweighted graph, k out of range, a bad
+ * source or NULL pointers.
+ */
+gbf_status gbf_mssp(gbf_graph *g, const int32_t *srcs, int32_t k, int32_t *dist, int mem,
+                    const gbf_options *opt, void *cuda_stream);
+
 #define GBF_TUNE_BFS 0   /* tune gbf_bfs */
 #define GBF_TUNE_MSBFS 1 /* tune gbf_msbfs (64 lanes) */
 #define GBF_TUNE_WBFS 2  /* tune gbf_wbfs */
@@ -356,8 +371,9 @@ gbf_status gbf_autotune(gbf_graph *g, int32_t kind, gbf_options *out);
  * pending BFS queries of one graph into one multi-source launch (8-bit lanes
  * for 2..8 queries, 64-bit lanes above; each lane writes its query's result
  * slot), or run a batch smaller than min_batch as single-source launches;
- * wBFS engines run one weighted query each.  Engines run concurrently on
- * equal shares of the GPU.
+ * wBFS engines coalesce up to 8 pending weighted queries of one graph into
+ * one gbf_mssp launch (a single one runs as gbf_wbfs).  Engines run
+ * concurrently on shares of the GPU.
  * Results stay on the device until polled.  The paper has no serving layer;
  * results are identical to the single-query calls.
  */
@@ -369,13 +385,20 @@ typedef struct gbf_server gbf_server;
 typedef struct {
   int32_t bfs_engines;   /* concurrent BFS batches (default 2) */
   int32_t wbfs_engines;  /* concurrent weighted queries (default 2; unused without weighted graphs) */
-  int32_t max_batch;     /* BFS queries per launch, 1..64 (default 64); 1 = one query per launch
-                            with the single-source BFS kernel */
+  int32_t max_batch;     /* BFS queries per launch, 1..64 (default 64), and weighted queries
+                            per launch, up to 8; 1 = one query per launch with the
+                            single-source kernels */
   int32_t max_queue;     /* pending queries before submit returns GBF_ERR_BUSY (default 65536) */
   size_t hbm_budget;     /* device bytes for result slots (0 = a quarter of free HBM) */
   gbf_options kernel;    /* kernel knobs (ctas is capped to the engine's share) */
   int32_t min_batch;     /* BFS batches with fewer queries run as single-source launches
                             (default 2) */
+  int32_t wbfs_share;    /* percent of the GPU's resident CTAs the weighted engines share
+                            (split evenly among them; the BFS engines share the rest);
+                            0 = every engine gets an equal share (default) */
+  int32_t always_batch;  /* 1 = batch whenever min_batch or more queries of a graph wait;
+                            0 = batch only where the measured GPU time per query is lower
+                            than one query per launch (default) */
   int32_t reserved;
 } gbf_server_options;
 

@@ -64,7 +64,8 @@ class gbf_server_options(ctypes.Structure):
     _fields_ = [("bfs_engines", ctypes.c_int32), ("wbfs_engines", ctypes.c_int32),
                 ("max_batch", ctypes.c_int32), ("max_queue", ctypes.c_int32),
                 ("hbm_budget", ctypes.c_size_t), ("kernel", gbf_options),
-                ("min_batch", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("min_batch", ctypes.c_int32), ("wbfs_share", ctypes.c_int32),
+                ("always_batch", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class gbf_server_counters(ctypes.Structure):
@@ -110,6 +111,7 @@ def _load() -> ctypes.CDLL:
         "gbf_kcore": (S, [P, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
         "gbf_wait": (S, [P, P, ctypes.POINTER(gbf_stats)]),
         "gbf_msbfs": (S, [P, P, I32, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
+        "gbf_mssp": (S, [P, P, I32, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
         "gbf_server_options_default": (S, [ctypes.POINTER(gbf_server_options)]),
         "gbf_server_create": (S, [P, I32, ctypes.POINTER(gbf_server_options), ctypes.POINTER(P)]),
         "gbf_server_submit": (S, [P, I32, I32, I32, ctypes.POINTER(U64)]),
@@ -294,6 +296,14 @@ def gbf_msbfs(h: int, srcs, dist, opt: Optional[gbf_options] = None, stream=None
            "gbf_msbfs")
 
 
+def gbf_mssp(h: int, srcs, dist, opt: Optional[gbf_options] = None, stream=None) -> None:
+    """Weighted shortest paths from k <= 8 sources into dist[k, n] (row i = source i)."""
+    s = np.ascontiguousarray(np.asarray(srcs, dtype=np.int32))
+    pd, mem = _ptr(dist)
+    _check(_lib.gbf_mssp(h, s.ctypes.data, int(s.size), pd, mem, _opt(opt), _stream(stream)),
+           "gbf_mssp")
+
+
 TUNE_BFS, TUNE_MSBFS, TUNE_WBFS = 0, 1, 2
 
 
@@ -452,6 +462,11 @@ class Graph:
     def msbfs(self, srcs, opt=None):
         d = np.empty((len(srcs), self.n), dtype=np.int32)
         gbf_msbfs(self.h, srcs, d, opt)
+        return d
+
+    def mssp(self, srcs, opt=None):
+        d = np.empty((len(srcs), self.n), dtype=np.int32)
+        gbf_mssp(self.h, srcs, d, opt)
         return d
 
     def wbfs(self, src: int, opt=None):

@@ -124,6 +124,11 @@ struct Workspace {
   void *bc_info = nullptr;
   int bc_max_levels = 0;
   double *bc_out_tmp = nullptr;
+  // multi-source SSSP (lazy): 8 distance lanes per vertex, 3 lane-mask arrays
+  // (a byte per vertex), output staging for host buffers
+  int32_t *mssp_dd = nullptr;
+  unsigned *mssp_imp = nullptr;
+  int32_t *mssp_out_tmp = nullptr;
   // pinned host copy of the control block
   Ctl *ctl_host = nullptr;
   int last_kind = 0;   // 1 bfs, 2 wbfs, 3 msbfs
@@ -183,6 +188,11 @@ int resident_ctas_per_sm_wbfs(const Opts &o, int nB);
 int resident_ctas_per_sm_msbfs(const Opts &o);
 gbf_status launch_msbfs_rows(Graph &g, Workspace &ws, const int32_t *srcs_host, int32_t k,
                              int32_t *const *rows, const Opts &o, cudaStream_t st);
+// Multi-source SSSP (mssp.cu): k <= 8 weighted sources, row i -> rows[i].
+gbf_status ws_ensure_mssp(Graph &g, Workspace &ws, bool host_out);
+gbf_status launch_mssp_rows(Graph &g, Workspace &ws, const int32_t *srcs_host, int32_t k,
+                            int32_t *const *rows, const Opts &o, cudaStream_t st);
+int resident_ctas_per_sm_mssp(const Opts &o);
 
 }  // namespace gbf
 

@@ -340,7 +340,8 @@ void ws_free(Workspace &ws) {
                   ws.slot_cnt, ws.ovf[0], ws.ovf[1], ws.ms_seen, ws.ms_visit, ws.ms_next,
                   ws.ms_q[2], ws.ms_qoff[2], ws.ms_cs[2], ws.ms_touched, ws.ms_call,
                   ws.ms_dist_tmp, ws.bc_paths, ws.bc_lvl, ws.bc_cs, ws.bc_info,
-                  ws.bc_out_tmp, ws.side[0], ws.side[1], ws.xround};
+                  ws.bc_out_tmp, ws.side[0], ws.side[1], ws.xround, ws.mssp_dd, ws.mssp_imp,
+                  ws.mssp_out_tmp};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (ws.ctl_host) cudaFreeHost(ws.ctl_host);

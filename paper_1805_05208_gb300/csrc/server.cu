@@ -5,15 +5,25 @@
 // from an HBM budget) and the pending queue has room; otherwise submit
 // returns GBF_ERR_BUSY.  A dispatcher thread keeps a set of engines busy,
 // each with its own CUDA stream and workspace:
-//   - BFS engines take up to max_batch pending BFS requests of one graph
-//     (the graph whose oldest request is oldest) and run them as one
-//     multi-source BFS launch (8-bit lanes for 2..8 requests, 64-bit lanes
-//     above) whose lane i writes straight into request i's result slot; a
-//     batch smaller than min_batch runs as single-source BFS launches back to
-//     back instead (and max_batch = 1 gives one query per launch);
-//   - wBFS engines take the oldest weighted request.
-// Engines run concurrently; each persistent launch gets an equal share of
-// the GPU's resident CTAs, so all engines' CTAs can be co-resident at once.
+//   - BFS engines take the pending BFS requests of one graph (the graph whose
+//     oldest request is oldest): up to max_batch of them as one multi-source
+//     BFS launch (8-bit lanes for 2..8 requests, 64-bit lanes above) whose
+//     lane i writes straight into request i's result slot, or a few as
+//     single-source launches back to back;
+//   - wBFS engines likewise: up to 8 weighted requests of one graph as one
+//     multi-source SSSP launch (distance lanes advanced by shared
+//     Bellman-Ford rounds), or single weighted BFS launches.
+// Whether to batch is decided per graph and kind from the GPU time each way
+// has taken per query so far (CUDA events around every launch, weighted to
+// the recent ones; a batch size class not yet measured is tried), so a
+// batch runs only where it is cheaper per query: on the large graphs a few
+// weighted queries cost more together than apart, on the small ones far
+// less.  Batches smaller than min_batch never run, and max_batch = 1 gives
+// one query per launch.
+// Engines run concurrently; each persistent launch gets a share of the GPU's
+// resident CTAs (equal shares, or wbfs_share percent for the weighted
+// engines together), and the shares add up to what fits at once, so all
+// engines' CTAs can be co-resident.
 // Results stay in their device slots until polled (copied to the caller or
 // dropped), which frees the slot.  Latency is measured from submit to the
 // dispatcher observing the launch's completion event.
@@ -55,11 +65,31 @@ struct Engine {
   Graph shape;  // sizing descriptor (max n, m, w) for the workspace
   Workspace ws;
   cudaStream_t st = nullptr;
-  cudaEvent_t done = nullptr;
+  cudaEvent_t start = nullptr, done = nullptr;
   bool busy = false;
   int graph = -1;
+  int cls = 0;       // cost class of the running work (see CostModel)
+  int launches = 1;  // launches it took
   std::vector<uint64_t> batch;
 };
+
+// Measured GPU time per launch (ms, exponentially weighted) of each way a
+// graph's queries of one kind can run: class 0 one query per launch, class
+// j >= 1 one multi-source launch of 2^(j-1) < k <= 2^j queries.
+constexpr int kCostClasses = 7;
+struct CostModel {
+  double ms[kCostClasses] = {0, 0, 0, 0, 0, 0, 0};
+  int seen[kCostClasses] = {0, 0, 0, 0, 0, 0, 0};
+  void add(int c, double v) {
+    ms[c] = seen[c] ? 0.7 * ms[c] + 0.3 * v : v;
+    seen[c]++;
+  }
+};
+inline int cost_class(int k) {
+  int j = 0;
+  while ((1 << j) < k) j++;
+  return k <= 1 ? 0 : j;
+}
 
 }  // namespace
 }  // namespace gbf
@@ -67,7 +97,7 @@ struct Engine {
 struct gbf_server {
   std::vector<gbf::Graph *> graphs;
   gbf_server_options opt;
-  gbf::Opts kopt_bfs, kopt_single, kopt_wbfs;
+  gbf::Opts kopt_bfs, kopt_single, kopt_wbfs, kopt_mssp;
   int32_t max_n = 0;
   char *slot_mem = nullptr;
   size_t slot_bytes = 0;
@@ -77,7 +107,8 @@ struct gbf_server {
   std::condition_variable cv;
   std::unordered_map<uint64_t, gbf::Request> reqs;
   std::vector<std::deque<uint64_t>> bfs_q;  // per graph
-  std::deque<uint64_t> wbfs_q;
+  std::vector<std::deque<uint64_t>> wbfs_q;  // per graph
+  std::vector<gbf::CostModel> cost[2];        // per kind, per graph
   uint64_t next_ticket = 1;
   size_t pending = 0;
   std::thread worker;
@@ -96,46 +127,40 @@ int32_t *slot_ptr(gbf_server *s, int slot) {
 
 // Launch work on an idle engine; caller holds s->mu.
 void dispatch(gbf_server *s, Engine *e) {
-  if (e->kind == GBF_QUERY_WBFS) {
-    if (s->wbfs_q.empty()) return;
-    const uint64_t t = s->wbfs_q.front();
-    s->wbfs_q.pop_front();
-    Request &r = s->reqs[t];
-    Graph &g = *s->graphs[r.graph];
-    r.state = 1;
-    e->batch.assign(1, t);
-    e->graph = r.graph;
-    gbf_status st = launch_wbfs(g, e->ws, r.src, slot_ptr(s, r.slot), s->kopt_wbfs, e->st);
-    if (st != GBF_OK) {
-      r.state = 3;
-      r.status = st;
-      r.t_done = Clock::now();
-      s->failed++;
-      s->pending--;
-      return;
-    }
-    cudaEventRecord(e->done, e->st);
-    e->busy = true;
-    return;
-  }
-  // BFS engine: the graph whose oldest pending request is oldest
+  // the graph whose oldest pending request of this engine's kind is oldest
+  auto &queues = e->kind == GBF_QUERY_WBFS ? s->wbfs_q : s->bfs_q;
   int best = -1;
   Clock::time_point oldest = Clock::time_point::max();
-  for (size_t gi = 0; gi < s->bfs_q.size(); gi++) {
-    if (s->bfs_q[gi].empty()) continue;
-    const Request &r = s->reqs[s->bfs_q[gi].front()];
+  for (size_t gi = 0; gi < queues.size(); gi++) {
+    if (queues[gi].empty()) continue;
+    const Request &r = s->reqs[queues[gi].front()];
     if (r.t_submit < oldest) {
       oldest = r.t_submit;
       best = (int)gi;
     }
   }
   if (best < 0) return;
-  auto &q = s->bfs_q[best];
-  const int kmax = std::max(1, std::min(64, s->opt.max_batch));
+  auto &q = queues[best];
+  Graph &g = *s->graphs[best];
+  const bool wk = e->kind == GBF_QUERY_WBFS;
+  // Batch or not: the largest batch the queue allows (up to 8 weighted, 64
+  // BFS queries), against one query per launch, by the measured GPU time
+  // per query of each on this graph; a way not measured yet is tried first.
+  const int cap = std::max(1, std::min(wk ? 8 : 64, s->opt.max_batch));
+  const int kb = std::min<int>(cap, (int)q.size());
+  bool batch = false;
+  if (kb >= std::max(2, s->opt.min_batch)) {
+    const CostModel &cm = s->cost[wk ? 1 : 0][best];
+    const int cb = cost_class(kb);
+    if (s->opt.always_batch || !cm.seen[cb]) batch = true;
+    else if (!cm.seen[0]) batch = false;
+    else batch = cm.ms[cb] / kb < cm.ms[0];
+  }
+  const int k = batch ? kb : std::min<int>((int)q.size(), 4);  // singles: a few back to back
   e->batch.clear();
   int32_t srcs[64];
   int32_t *rows[64];
-  while (!q.empty() && (int)e->batch.size() < kmax) {
+  while ((int)e->batch.size() < k) {
     const uint64_t t = q.front();
     q.pop_front();
     Request &r = s->reqs[t];
@@ -145,15 +170,17 @@ void dispatch(gbf_server *s, Engine *e) {
     e->batch.push_back(t);
   }
   e->graph = best;
-  Graph &g = *s->graphs[best];
-  gbf_status st;
-  const int k = (int)e->batch.size();
-  if (kmax == 1 || k < s->opt.min_batch) {
-    st = GBF_OK;
-    for (int i = 0; i < k && st == GBF_OK; i++)
-      st = launch_bfs(g, e->ws, srcs[i], rows[i], nullptr, s->kopt_single, e->st);
+  e->cls = batch ? cost_class(k) : 0;
+  e->launches = batch ? 1 : k;
+  cudaEventRecord(e->start, e->st);
+  gbf_status st = GBF_OK;
+  if (batch) {
+    st = wk ? launch_mssp_rows(g, e->ws, srcs, (int32_t)k, rows, s->kopt_mssp, e->st)
+            : launch_msbfs_rows(g, e->ws, srcs, (int32_t)k, rows, s->kopt_bfs, e->st);
   } else {
-    st = launch_msbfs_rows(g, e->ws, srcs, (int32_t)k, rows, s->kopt_bfs, e->st);
+    for (int i = 0; i < k && st == GBF_OK; i++)
+      st = wk ? launch_wbfs(g, e->ws, srcs[i], rows[i], s->kopt_wbfs, e->st)
+              : launch_bfs(g, e->ws, srcs[i], rows[i], nullptr, s->kopt_single, e->st);
   }
   if (st != GBF_OK) {
     for (uint64_t t : e->batch) {
@@ -167,8 +194,10 @@ void dispatch(gbf_server *s, Engine *e) {
     e->batch.clear();
     return;
   }
-  s->batches++;
-  s->batched_queries += e->batch.size();
+  if (!wk) {
+    s->batches += batch ? 1 : k;
+    s->batched_queries += e->batch.size();
+  }
   cudaEventRecord(e->done, e->st);
   e->busy = true;
 }
@@ -190,6 +219,9 @@ void worker_loop(gbf_server *s) {
       } else {
         gbf_stats sts;
         st = ws_collect(e->ws, e->st, &sts);
+        float ms = 0.f;
+        if (st == GBF_OK && cudaEventElapsedTime(&ms, e->start, e->done) == cudaSuccess)
+          s->cost[e->kind == GBF_QUERY_WBFS ? 1 : 0][e->graph].add(e->cls, ms / e->launches);
       }
       for (uint64_t t : e->batch) {
         auto it = s->reqs.find(t);
@@ -222,6 +254,7 @@ void destroy_engine(Engine *e) {
   if (e->st) cudaStreamSynchronize(e->st);
   ws_free(e->ws);
   if (e->done) cudaEventDestroy(e->done);
+  if (e->start) cudaEventDestroy(e->start);
   if (e->st) cudaStreamDestroy(e->st);
   delete e;
 }
@@ -279,6 +312,9 @@ gbf_status gbf_server_create(gbf_graph *const *graphs, int32_t ngraphs,
   }
   s->device = s->graphs[0]->device;
   s->bfs_q.resize(ngraphs);
+  s->wbfs_q.resize(ngraphs);
+  s->cost[0].resize(ngraphs);
+  s->cost[1].resize(ngraphs);
   auto fail = [&](gbf_status st) {
     gbf_server_destroy(s);
     return st;
@@ -313,11 +349,13 @@ gbf_status gbf_server_create(gbf_graph *const *graphs, int32_t ngraphs,
     sh.num_sms = sms;
     if ((e = cudaStreamCreateWithFlags(&en->st, cudaStreamNonBlocking)) != cudaSuccess)
       return fail(cuda_fail(e, "engine stream"));
-    if ((e = cudaEventCreateWithFlags(&en->done, cudaEventDisableTiming)) != cudaSuccess)
+    if ((e = cudaEventCreate(&en->start)) != cudaSuccess || (e = cudaEventCreate(&en->done)) != cudaSuccess)
       return fail(cuda_fail(e, "engine event"));
     gbf_status st;
-    if (en->kind == GBF_QUERY_WBFS)
+    if (en->kind == GBF_QUERY_WBFS) {
       st = ws_ensure_wbfs(sh, en->ws, (int)std::min<uint32_t>(std::max<uint32_t>(max_w + 1, 2), 256));
+      if (st == GBF_OK && s->opt.max_batch > 1) st = ws_ensure_mssp(sh, en->ws, false);
+    }
     else if (s->opt.max_batch > 1) st = ws_ensure_msbfs(sh, en->ws, false);
     else st = ws_ensure_base(sh, en->ws);
     if (st != GBF_OK) return fail(st);
@@ -329,18 +367,30 @@ gbf_status gbf_server_create(gbf_graph *const *graphs, int32_t ngraphs,
   s->kopt_bfs = resolve(&ko, *s->graphs[0], s->opt.max_batch > 1 ? GBF_TUNE_MSBFS : GBF_TUNE_BFS);
   s->kopt_single = resolve(&ko, *s->graphs[0], GBF_TUNE_BFS);
   s->kopt_wbfs = resolve(&ko, *s->graphs[0], GBF_TUNE_WBFS);
+  s->kopt_mssp = resolve(&ko, *s->graphs[0], GBF_TUNE_BFS);
   {
     int per_sm = resident_ctas_per_sm_bfs(s->kopt_single);
     if (s->opt.max_batch > 1) per_sm = std::min(per_sm, resident_ctas_per_sm_msbfs(s->kopt_bfs));
     if (any_w && s->opt.wbfs_engines > 0) {
       const int nB = (int)std::min<uint32_t>(std::max<uint32_t>(max_w + 1, 2), 256);
       per_sm = std::min(per_sm, resident_ctas_per_sm_wbfs(s->kopt_wbfs, nB));
+      if (s->opt.max_batch > 1) per_sm = std::min(per_sm, resident_ctas_per_sm_mssp(s->kopt_mssp));
     }
     if (per_sm < 1) return fail((set_error("kernels do not fit on an SM"), GBF_ERR_INVALID));
-    const int share = std::max(1, (sms * per_sm) / nengines);
-    if (s->kopt_bfs.ctas == 0 || s->kopt_bfs.ctas > share) s->kopt_bfs.ctas = share;
-    if (s->kopt_single.ctas == 0 || s->kopt_single.ctas > share) s->kopt_single.ctas = share;
-    if (s->kopt_wbfs.ctas == 0 || s->kopt_wbfs.ctas > share) s->kopt_wbfs.ctas = share;
+    const int total = sms * per_sm;
+    int bshare = std::max(1, total / nengines), wshare = bshare;
+    const int nw = any_w ? s->opt.wbfs_engines : 0, nb = s->opt.bfs_engines;
+    if (s->opt.wbfs_share > 0 && nw > 0 && nb > 0) {
+      // the weighted engines together get wbfs_share percent, the rest goes
+      // to the BFS engines; the shares still add up to what fits at once
+      const int wtot = std::min(total - nb, std::max(nw, total * std::min(s->opt.wbfs_share, 99) / 100));
+      wshare = std::max(1, wtot / nw);
+      bshare = std::max(1, (total - wshare * nw) / nb);
+    }
+    if (s->kopt_bfs.ctas == 0 || s->kopt_bfs.ctas > bshare) s->kopt_bfs.ctas = bshare;
+    if (s->kopt_single.ctas == 0 || s->kopt_single.ctas > bshare) s->kopt_single.ctas = bshare;
+    if (s->kopt_wbfs.ctas == 0 || s->kopt_wbfs.ctas > wshare) s->kopt_wbfs.ctas = wshare;
+    if (s->kopt_mssp.ctas == 0 || s->kopt_mssp.ctas > wshare) s->kopt_mssp.ctas = wshare;
   }
   s->worker = std::thread(worker_loop, s);
   *out = s;
@@ -376,7 +426,7 @@ gbf_status gbf_server_submit(gbf_server *s, int32_t graph_idx, int32_t kind, int
   r.status = GBF_OK;
   s->reqs.emplace(r.ticket, r);
   if (kind == GBF_QUERY_BFS) s->bfs_q[graph_idx].push_back(r.ticket);
-  else s->wbfs_q.push_back(r.ticket);
+  else s->wbfs_q[graph_idx].push_back(r.ticket);
   s->pending++;
   *ticket = r.ticket;
   s->cv.notify_all();

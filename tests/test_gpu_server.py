@@ -49,15 +49,18 @@ def _expected(csr, kind, s):
     return oracle.bfs(csr, s, parents=False)[0] if kind == 0 else oracle.dijkstra(csr, s)
 
 
-@pytest.mark.parametrize("max_batch,min_batch", [(64, 8), (1, 8), (64, 0), (64, 65)])
-def test_served_equals_alone(gb, graphs, max_batch, min_batch):
-    """min_batch 0: every batch runs as one 64-lane launch; 65: every batch
-    runs as single-source launches; 8: small batches single, large ones
-    packed."""
+@pytest.mark.parametrize("max_batch,min_batch,always", [(64, 8, 0), (1, 8, 0), (64, 0, 1),
+                                                          (64, 65, 0), (64, 2, 0), (8, 2, 1)])
+def test_served_equals_alone(gb, graphs, max_batch, min_batch, always):
+    """always 1 with min_batch 0: every batch of two or more queries runs as
+    one multi-source launch (BFS lanes, weighted SSSP lanes); min_batch 65:
+    every query runs alone; otherwise batches run where their measured cost
+    per query is lower; max_batch 1: one query per launch."""
     hs = [gb.Graph(c) for c in graphs]
     srv = gb.gbf_server_create([h.h for h in hs],
                                gb.gbf_server_options_default(max_batch=max_batch,
                                                              min_batch=min_batch,
+                                                             always_batch=always,
                                                              hbm_budget=64 << 20))
     rng = np.random.default_rng(7)
     queries = {}
