@@ -82,6 +82,13 @@ WORKLOADS = {
                               "RMAT scale 24 ef16, autotuned; vs 64 single-source BFS launches"),
     "msbfs-rmat20": dict(kind="msbfs", graph="rmat", scale=20, ef=16, w=None, nsrc=64,
                          desc="multi-source BFS, 64 sources, RMAT scale 20 (profiling size)"),
+    "mssp-rmat22": dict(kind="mssp", graph="rmat", scale=22, ef=16, w=(1, 22), nsrc=8,
+                        desc="multi-source SSSP, 8 seeded sources in one launch (8 distance lanes, "
+                             "shared Bellman-Ford rounds), RMAT scale 22 ef16, w in [1,22); vs the "
+                             "8 queries as single-source weighted BFS launches"),
+    "mssp-rmat20": dict(kind="mssp", graph="rmat", scale=20, ef=16, w=(1, 22), nsrc=8,
+                        desc="multi-source SSSP, 8 sources in one launch, RMAT scale 20 ef16, "
+                             "w in [1,22)"),
     "serve": dict(kind="serve", graph="rmat", scales=(18, 20, 22, 24), ef=16, w=(1, 22), nsrc=0,
                   rates=(1000, 2000, 5000, 10000, 20000, 50000), warm=2000, meas=20000,
                   desc="serving: 4 resident RMAT graphs (scales 18/20/22/24, ef16, w in [1,22)), "
@@ -139,7 +146,7 @@ def make_sources(g, wl, rank=0):
     return G.sources(g, k, seed=3 + 1000 * rank)
 
 
-ORACLE_NAME = {"bfs": "FIFO BFS", "msbfs": "FIFO BFS per source", "wbfs": "binary-heap Dijkstra", "delta": "binary-heap Dijkstra",
+ORACLE_NAME = {"bfs": "FIFO BFS", "msbfs": "FIFO BFS per source", "mssp": "binary-heap Dijkstra per source", "wbfs": "binary-heap Dijkstra", "delta": "binary-heap Dijkstra",
                "ldd": "MPX rounds", "cc": "FIFO search per component",
                "bf": "frontier Bellman-Ford", "widest": "(max,min) Bellman-Ford rounds",
                "bc": "betweenness forward + backward passes", "kcore": "bucket peeling"}
@@ -224,6 +231,7 @@ KERNEL_SOURCES = {
     "bf_kernel": ("bellman_ford.cu", "dev_common.cuh", "gbf_impl.h"),
     "bc_kernel": ("betweenness.cu", "dev_common.cuh", "gbf_impl.h"),
     "kcore_kernel": ("kcore.cu", "dev_common.cuh", "gbf_impl.h"),
+    "mssp_kernel": ("mssp.cu", "dev_common.cuh", "gbf_impl.h"),
     "ldd_kernel": ("ldd.cu", "dev_common.cuh", "gbf_impl.h"),
     "cc_kernel": ("connectivity.cu", "dev_common.cuh", "gbf_impl.h"),
 }
@@ -328,6 +336,13 @@ def bytes_model(kind, n, st):
         # target, weight, source value, target value (16); per successful
         # writeMin/Max: the atomic and the flag test-and-set (8)
         return 4 * n + n // 4 + 16 * V + 16 * E + 8 * R
+    if kind == "mssp":
+        # init and final read of the 8 distance lanes (2 x 32n), every row
+        # written once (4kn, k = 8); per scanned arc: target, weight and the
+        # target's 32-byte lane sector (40); per frontier vertex: queue entry,
+        # prefix, first arc and its lane byte (16); per successful writeMin:
+        # the atomic and the lane-mask OR (8)
+        return 64 * n + 32 * n + 40 * E + 16 * V + 8 * R
     if kind == "msbfs":
         # init seen/visit/next (32n); every dist[i][v] written once (4kn); per
         # scanned arc: target + the neighbour's lane word (12); per frontier
@@ -378,7 +393,7 @@ def cpu_reference_sample(g, wl, srcs, budget_s=15.0, max_queries=None):
     done = 0
     for s in srcs:
         t0 = time.perf_counter()
-        if wl["kind"] in ("wbfs", "delta"):
+        if wl["kind"] in ("wbfs", "delta", "mssp"):
             d = oracle.dijkstra(g, int(s))
         elif wl["kind"] == "bf":
             d = oracle.bellman_ford(g, int(s))
@@ -837,6 +852,108 @@ def run_msbfs(args, wl, g, srcs, graph, opt, stream, dev, rank, world, barrier, 
     return 0
 
 
+def run_mssp(args, wl, g, srcs, graph, opt, stream, dev, rank, world, barrier, dist_mod):
+    """One step = one multi-source SSSP launch over the 8 sources; the same
+    8 queries as single-source weighted BFS launches are timed beside it."""
+    import torch
+    import paper_1805_05208_gb300 as gb
+    n, k = g.n, len(srcs)
+    out = torch.empty((k, n), dtype=torch.int32, device=dev)
+    deg = torch.from_numpy(np.diff(g.off.astype(np.int64))).to(dev)
+    stats = trace0 = None
+    for w in range(args.warmup):
+        gb.gbf_mssp(graph.h, srcs, out, opt, stream)
+        if w == 0:
+            stats = gb.gbf_wait(graph.h, stream)
+            trace0 = gb.gbf_trace(graph.h)
+    gb.gbf_wait(graph.h, stream)
+    te_step = int(((out != INF).to(torch.int64) * deg).sum().item() // 2)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for s_ in range(args.steps):
+            ev[s_][0].record(stream)
+            gb.gbf_mssp(graph.h, srcs, out, opt, stream)
+            ev[s_][1].record(stream)
+        t1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    st = gb.gbf_wait(graph.h, stream)
+    if st["device_error"]:
+        raise RuntimeError(f"device error {st['device_error']}")
+    ms_total = t0.elapsed_time(t1)
+    # the comparison: the same queries as one weighted BFS launch each
+    d1 = torch.empty(n, dtype=torch.int32, device=dev)
+    for s_ in srcs[:2]:
+        gb.gbf_wbfs(graph.h, int(s_), d1, opt, stream)
+    torch.cuda.synchronize()
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for s_ in srcs:
+        gb.gbf_wbfs(graph.h, int(s_), d1, opt, stream)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    ms_single = a0.elapsed_time(a1)
+    if world > 1:
+        ms_total, te_all = reduce_job(ms_total, te_step, dist_mod, dev)
+    else:
+        te_all = float(te_step)
+    value = te_all * args.steps / (ms_total / 1e3) / 1e9
+    launch_ms = [e[0].elapsed_time(e[1]) for e in ev]
+    avg = sum(launch_ms) / len(launch_ms)
+    peak, peak_kind = load_peaks()
+    bpl = bytes_model("mssp", n, stats)
+    host = torch.empty((k, n), dtype=torch.int32, pin_memory=True).numpy()
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    barrier()
+    tt0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        gb.gbf_mssp(graph.h, srcs, host, opt, None)
+    e2e_s = time.perf_counter() - tt0
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            te_c, t_c, q = cpu_reference_sample(g, wl, srcs, budget_s=args.cpu_budget)
+            cpu = {"value": te_c / t_c / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                   "host": host_cpu(),
+                   "sample": f"{q} of the {k} single-source Dijkstra runs of one step, {t_c:.1f} s"}
+        clocks = clk.summary()
+        line = {
+            "metric": "GTEPS", "value": value, "unit": "GTEPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": workload_config(args.workload, wl, g, k),
+            "vs_single_source_launches": {"ms_8_wbfs": ms_single, "ms_one_mssp": ms_total / args.steps,
+                                          "speedup": ms_single / (ms_total / args.steps)},
+            "roofline": {"bound": "hbm", "kernel": "mssp_kernel", "achieved": bpl / (avg / 1e3) / 1e9,
+                         "peak": peak, "unit": "GB/s", "frac": bpl / (avg / 1e3) / 1e9 / peak,
+                         "peak_source": f"{peak_kind} hbm_gbs (burst copy)", "bytes_per_launch": bpl,
+                         "avg_launch_ms": avg, "model": EXT_MODEL,
+                         "traffic": measured_traffic(args.workload, "mssp_kernel")},
+            "cpu_baseline": cpu,
+            "e2e": {"value": te_all * e2e_steps / e2e_s / 1e9, "unit": "GTEPS",
+                    "h2d_bytes_per_step": 4 * k, "d2h_bytes_per_step": 4 * k * n},
+            "gpu_launches": args.steps,
+            "clocks": {kk: clocks[kk] for kk in ("sm_mhz", "sm_max_mhz", "reasons")},
+            "stats": {"rounds": stats["rounds"], "edges_scanned": stats["edges_scanned"],
+                      "per_query": [{f: stats[f] for f in STAT_TERMS}],
+                      "traversed_edges_per_step": te_step, "grid_ctas": stats["grid_ctas"],
+                      "block": stats["block"], "query0_trace": trace_summary(trace0)},
+        }
+        print(json.dumps(line))
+    graph.close()
+    if world > 1:
+        dist_mod.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -893,6 +1010,8 @@ def main():
     kind = wl["kind"]
     if kind == "msbfs":
         return run_msbfs(args, wl, g, srcs, graph, opt, stream, dev, rank, world, barrier, dist_mod)
+    if kind == "mssp":
+        return run_mssp(args, wl, g, srcs, graph, opt, stream, dev, rank, world, barrier, dist_mod)
     out_dtype = torch.float64 if kind == "bc" else torch.int32
     outs = [torch.empty(n, dtype=out_dtype, device=dev) for _ in srcs]
     if kind == "ldd":  # the shifts are an input; the join rounds a second output

@@ -24,10 +24,11 @@
 //
 // Graph-side arrays used when the graph provides them: a bitmap of the
 // vertices of degree 0 (they start out visited, so no dense level looks at
-// them) and the target of every vertex's first arc (`f1`): when the frontier
-// holds more than an eighth of all arcs, the dense step checks that arc from
-// a coalesced stream before it touches the vertex's adjacency list, which is
-// the sequential scan's first step read from a copy.
+// them) and the target of every vertex's first arc (`f1`; graph creation puts
+// the arc to the highest-degree neighbour first): when the frontier holds
+// more than an eighth of all arcs, or is made of hubs, the dense step checks
+// that arc from a coalesced stream before it touches the vertex's adjacency
+// list, which is the sequential scan's first step read from a copy.
 //
 // Readings of Alg. 1 used here: the source is marked visited with D = 0 and
 // vertices first reached while expanding level k-1 get D = k.  A vertex of
@@ -852,9 +853,13 @@ __global__ void __launch_bounds__(1024) bfs_kernel(BfsParams P) {
         count_bitmap(P, fout, outc, S);
       }
     } else {
-      // the first-arc check pays when a random arc leads into the frontier
-      // often: its chance is about the frontier's share of all arcs
-      const int32_t *f1 = (unsigned long long)D * 8ull > g.m ? P.f1 : nullptr;
+      // the first-arc check pays when a candidate's first arc (the arc to its
+      // highest-degree neighbour) leads into the frontier often: when the
+      // frontier holds more than an eighth of all arcs, or when its vertices
+      // average more than 8 times the graph's mean degree (a frontier of hubs)
+      const bool hubs = (unsigned long long)D * (unsigned)g.n >
+                        8ull * (unsigned long long)g.m * (unsigned long long)cnt;
+      const int32_t *f1 = ((unsigned long long)D * 8ull > g.m || hubs) ? P.f1 : nullptr;
       pull_level(P, S, fin, fout, f1, direct, level, outc, scanned, reached, pulled, bem++);
     }
     if (!grid_sync(ctl, bar, &s_flag)) break;

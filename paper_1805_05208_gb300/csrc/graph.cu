@@ -167,6 +167,44 @@ __global__ void k_digest(int32_t n, uint32_t m, const uint32_t *off, const int32
   }
 }
 
+// Each vertex's arc to its highest-degree neighbour is moved to the front of
+// its list (swapped with the first arc; the lowest position wins ties), so
+// that the first arc of every vertex, and the dense step's first-arc check
+// (f1), lead to the neighbour most likely to be on an early frontier.  The
+// order of a vertex's arcs carries no meaning for any query; the weights
+// move with their arcs.  A warp per vertex.
+__global__ void k_hub_first(int32_t n, const uint32_t *off, int32_t *tgt, uint32_t *w) {
+  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t tw = (gridDim.x * blockDim.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  for (uint32_t v = gw; v < (uint32_t)n; v += tw) {
+    const uint32_t s = off[v], e = off[v + 1];
+    if (e - s < 2) continue;
+    unsigned long long best = 0;  // (degree << 32) | ~position: larger is better
+    for (uint32_t k = s + lane; k < e; k += 32) {
+      const int32_t t = tgt[k];
+      const uint32_t d = off[t + 1] - off[t];
+      const unsigned long long key = ((unsigned long long)d << 32) | (0xffffffffu - (k - s));
+      if (key > best) best = key;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long y = __shfl_xor_sync(0xffffffffu, best, o);
+      if (y > best) best = y;
+    }
+    const uint32_t j = s + (0xffffffffu - (uint32_t)best);
+    if (lane == 0 && j != s) {
+      const int32_t t0 = tgt[s];
+      tgt[s] = tgt[j];
+      tgt[j] = t0;
+      if (w) {
+        const uint32_t w0 = w[s];
+        w[s] = w[j];
+        w[j] = w0;
+      }
+    }
+  }
+}
+
 // Per-vertex arrays derived from the CSR: bit v of leaf[] is set iff vertex
 // v has degree exactly 1, bit v of iso[] iff it has degree 0, and f1[v] is
 // the target of v's first arc (-1 without arcs).
@@ -490,6 +528,7 @@ gbf_status gbf_graph_create(int32_t n, const uint32_t *off, const int32_t *tgt, 
   }
   if (haux.flags == 0) {
     k_digest<<<grid, 256, 0, st>>>(n, m, g.off, g.tgt, g.w, &aux->sum, &aux->wmax);
+    k_hub_first<<<grid, 256, 0, st>>>(n, g.off, g.tgt, g.w);
     k_leaf<<<grid, 256, 0, st>>>(n, g.off, g.tgt, g.leaf, g.iso, g.f1);
   }
   e = cudaStreamSynchronize(st);
