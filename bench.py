@@ -55,6 +55,8 @@ WORKLOADS = {
                        desc="BFS (dist+parent), RMAT scale 20 ef16, 8 seeded sources (profiling size)"),
     "bfs-rmat22": dict(kind="bfs", graph="rmat", scale=22, ef=16, w=None, nsrc=8,
                        desc="BFS (dist+parent), RMAT scale 22 ef16, 8 seeded sources"),
+    "bfs-rmat24": dict(kind="bfs", graph="rmat", scale=24, ef=16, w=None, nsrc=4,
+                       desc="BFS (dist+parent), RMAT scale 24 ef16, 4 seeded sources (profiling size)"),
     "bfs-rmat26": dict(kind="bfs", graph="rmat", scale=26, ef=16, w=None, nsrc=4,
                        desc="BFS (dist+parent), RMAT scale 26 ef16 (~2.1B arcs), 4 seeded sources"),
     "bf-rmat22": dict(kind="bf", graph="rmat", scale=22, ef=16, w=(1, 22), nsrc=8,
