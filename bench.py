@@ -375,7 +375,7 @@ def trace_summary(tr):
     """Per-kind round counts and device time of one query's round trace."""
     out, prev = {}, 0
     names = {1: "sparse", 2: "dense", 3: "sparse+heavy", 4: "conversion+sparse", 5: "bucket",
-             6: "sparse-bitmap", 7: "conversion+sparse-bitmap"}
+             6: "sparse-bitmap", 7: "conversion+sparse-bitmap", 8: "cta-local"}
     for (_, kind, fr, fe, t, _tm) in tr:
         k = names.get(kind, str(kind))
         d = out.setdefault(k, {"rounds": 0, "us": 0.0, "frontier": 0})

@@ -85,7 +85,11 @@ typedef struct gbf_graph gbf_graph;
  *                 (1..256, default min(max weight + 1, 256); values <= max weight use the overflow bucket)
  *   dense_wbfs    1 = let wBFS switch to a dense edgeMap for dense buckets (default 0)
  *   spin_cap_us   time limit of every bounded device wait, microseconds (default 5,000,000)
- *   counters      reserved (statistics are always collected)
+ *   local_arcs    wBFS: a bucket of at most `block` entries whose live entries hold at most
+ *                 local_arcs arcs (1 .. 2^20 - 1) is expanded by one CTA alone, and so are
+ *                 the buckets after it while they stay that small, with CTA barriers only,
+ *                 while the other CTAs wait at one grid barrier (0 or negative = off, the
+ *                 default: on the measured graphs the kernel with this mode is slower)
  *   ctas          CTAs of the persistent kernels (default: every CTA that fits, all SMs;
  *                 on graphs with fewer than 8 arcs per vertex, whose many thin rounds
  *                 cost mostly their grid barrier, half as many CTAs as SMs)
@@ -104,7 +108,7 @@ typedef struct {
   int32_t heavy_cutoff;
   int32_t bucket_window;
   int32_t dense_wbfs;
-  int32_t counters;
+  int32_t local_arcs;
   int64_t spin_cap_us;
   int32_t ctas;
   int32_t pull_serial;
@@ -129,7 +133,7 @@ typedef struct {
   int32_t grid_ctas;         /* CTAs of the persistent launch */
   int32_t block;             /* threads per CTA */
   int32_t device_error;      /* gbf_status reported by the device */
-  int32_t reserved;
+  int32_t local_rounds;      /* wBFS: bucket rounds expanded by one CTA alone (local_arcs) */
 } gbf_stats;
 
 /* Fills *opt with the defaults (all knobs explicit). */
@@ -456,7 +460,8 @@ typedef struct {
   int32_t kind;           /* 1 sparse, 2 dense, 3 sparse + heavy pass, 4 conversion
                              (BFS: bitmap -> queue, then sparse), 5 k-core bucket pass
                              (frontier = the bucket), 6 BFS sparse level writing a
-                             bitmap, 7 the same after a bitmap -> queue conversion */
+                             bitmap, 7 the same after a bitmap -> queue conversion,
+                             8 wBFS bucket round expanded by one CTA alone */
   uint32_t frontier;      /* frontier vertices (wBFS: bucket entries, stale ones included) */
   uint32_t frontier_edges;/* out-degree sum of the frontier when known (0 otherwise) */
   int64_t t_ns;           /* device time at the end of the round, since the kernel started */

@@ -39,7 +39,7 @@ class GbfError(RuntimeError):
 class gbf_options(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int32), ("pull_divisor", ctypes.c_int32),
                 ("heavy_cutoff", ctypes.c_int32), ("bucket_window", ctypes.c_int32),
-                ("dense_wbfs", ctypes.c_int32), ("counters", ctypes.c_int32),
+                ("dense_wbfs", ctypes.c_int32), ("local_arcs", ctypes.c_int32),
                 ("spin_cap_us", ctypes.c_int64), ("ctas", ctypes.c_int32),
                 ("pull_serial", ctypes.c_int32), ("inject_wait", ctypes.c_int32),
                 ("pull_stay", ctypes.c_int32)]
@@ -54,10 +54,10 @@ class gbf_stats(ctypes.Structure):
                 ("vertices_pulled", ctypes.c_int64), ("device_ns", ctypes.c_int64),
                 ("grid_ctas", ctypes.c_int32),
                 ("block", ctypes.c_int32), ("device_error", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("local_rounds", ctypes.c_int32)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class gbf_server_options(ctypes.Structure):

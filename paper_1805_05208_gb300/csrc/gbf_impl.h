@@ -51,12 +51,18 @@ struct Ctl {
   unsigned long long inserts;
   unsigned long long heavy;
   unsigned long long pulled;   // dense-round candidates
-  int rounds, push_rounds, pull_rounds, refills;
+  int rounds, push_rounds, pull_rounds, refills, local_rounds;
+  // wBFS: bucket state CTA 0 hands back after a run of CTA-local rounds
+  int loc_t, loc_lo;
+  unsigned int loc_pend[8];
+  unsigned int loc_base[256];
 };
 
 // One record per round of a persistent launch, written by CTA 0 after the
 // round's last barrier (kind: 1 sparse, 2 dense, 3 sparse + heavy pass,
-// 4 conversion); t_ns is %globaltimer time since the kernel started.
+// 4 conversion, 5 k-core bucket pass, 6 / 7 BFS levels writing a bitmap,
+// 8 wBFS round of one CTA alone); t_ns is %globaltimer time since the
+// kernel started.
 struct TraceRec {
   int32_t round;
   int32_t kind;
@@ -158,6 +164,7 @@ struct Graph {
 struct Opts {
   int block, pull_divisor, heavy_cutoff, bucket_window, dense_wbfs, ctas, pull_serial, inject_wait;
   int pull_stay;  // BFS: after a dense level, stay dense while |F| * pull_stay > n (0: off)
+  int local_arcs; // wBFS: arcs of a bucket one CTA expands alone (0: off)
   long long spin_cap_ns;
 };
 Opts resolve(const gbf_options *o, const Graph &g, int kind);  // kind: GBF_TUNE_*

@@ -73,6 +73,8 @@ Opts resolve(const gbf_options *o, const Graph &g, int kind) {
   // pull_stay 0: default 24 (after a dense level, the next stays dense while
   // the frontier holds more than n / 24 vertices); negative: off
   r.pull_stay = o->pull_stay > 0 ? o->pull_stay : (o->pull_stay < 0 ? 0 : 24);
+  // local_arcs: off unless positive (below the 20-bit degree field)
+  r.local_arcs = o->local_arcs > 0 ? std::min(o->local_arcs, (1 << 20) - 1) : 0;
   long long us = o->spin_cap_us > 0 ? o->spin_cap_us : d.spin_cap_us;
   r.spin_cap_ns = us * 1000LL;
   return r;
@@ -412,6 +414,7 @@ gbf_status ws_collect(Workspace &ws, cudaStream_t st, gbf_stats *stats) {
     stats->grid_ctas = ws.last_grid;
     stats->block = ws.last_block;
     stats->device_error = c.err;
+    stats->local_rounds = c.local_rounds;
   }
   if (c.err != 0) {
     char buf[128];

@@ -77,6 +77,7 @@ struct WbfsParams {
   int cap;
   int log2_bmax_fine;
   int heavy;
+  int local_arcs;  // CTA-local rounds: most live arcs of a bucket one CTA expands alone
   int inject_wait;
   long long cap_ns;
   // Δ-stepping (dl > 0): buckets hold distance ranges [qΔ, (q+1)Δ), Δ = 2^dl;
@@ -112,6 +113,7 @@ struct FileSink {
   int32_t *sq;       // this round's side list, its flag bitmap and count
   uint32_t *sfl;
   unsigned *scnt;
+  uint32_t *cnt_out;  // CTA-local rounds: the CTA's copy of the slot counters, kept current
 
   __device__ __forceinline__ void append(PushSmem &S, bool low, int32_t v, uint32_t ndu) {
     const unsigned bal = __ballot_sync(kFull, low);
@@ -149,9 +151,13 @@ struct FileSink {
       if (gp < (uint32_t)P->g.n) sq[gp] = v;
       else raise_error(P->ctl, GBF_ERR_OVERFLOW, 13);
     } else if (sl >= 0) {
-      const uint32_t gp = atomicAdd(P->slot_cnt + sl, 1u) % (uint32_t)P->g.n;
-      P->slots[(size_t)sl * (size_t)P->g.n + gp] = v;
+      const uint32_t raw = atomicAdd(P->slot_cnt + sl, 1u);
+      P->slots[(size_t)sl * (size_t)P->g.n + raw % (uint32_t)P->g.n] = v;
       atomicOr(imask + (sl >> 5), 1u << (sl & 31));
+      if (cnt_out) {  // CTA-local round: the filed mask and counter of this CTA alone
+        atomicOr(s_pub + (sl >> 5), 1u << (sl & 31));
+        atomicMax(cnt_out + sl, raw + 1u);
+      }
     } else {
       const uint32_t gp = atomicAdd(&P->ctl->ovf_cnt[cur], 1u);
       if (gp < P->ovf_cap) {
@@ -246,6 +252,7 @@ struct FileSink {
       const uint32_t h = S.hist[i];
       if (h) {
         S.gbase[i] = atomicAdd(P->slot_cnt + i, h);
+        if (cnt_out) cnt_out[i] = S.gbase[i] + h;
         const unsigned bit = 1u << (i & 31);
         if (!(s_pub[i >> 5] & bit)) {
           atomicOr(s_pub + (i >> 5), bit);
@@ -424,8 +431,37 @@ __device__ int32_t next_bucket(const unsigned *s_pend, int nB, int32_t lo, int *
 __host__ __device__ inline SmemShape wbfs_smem_shape(int bmax, int cap, int nB) {
   return SmemShape{bmax, cap, 1, nB + 1};
 }
+// Dynamic shared memory: the edgeMap stage, then per ring slot the consumed
+// position and the append counter as read after the last barrier.
+__host__ __device__ inline size_t wbfs_smem_bytes(int bmax, int cap, int nB) {
+  return push_smem_bytes(wbfs_smem_shape(bmax, cap, nB)) + 2 * sizeof(uint32_t) * (size_t)nB;
+}
 
-template <bool kDelta>
+// What round t + 1 starts from, read in one batch after the barrier that
+// completes round t's filings (with whatever else the caller loads there):
+// the slots filed in round t (mask t % 3; this thread's word), the length of
+// round t's side list (Δ-stepping) and every slot's append counter.  The
+// counter of the slot that round t + 1 consumes is final here: no round
+// files into its own bucket's slot.
+struct RoundState {
+  unsigned mask;
+  uint32_t side;
+};
+__device__ __forceinline__ RoundState read_round_state(const WbfsParams &P, int t, uint32_t *s_cnt) {
+  RoundState r{0u, 0u};
+  if (threadIdx.x < kMaskWords) r.mask = ld_vol(P.ctl->imask[t % 3][threadIdx.x]);
+  if (P.dl > 0) r.side = ld_vol(P.ctl->scnt[t % 3]);
+  for (int i = threadIdx.x; i < P.nB; i += blockDim.x) s_cnt[i] = ld_vol(P.slot_cnt[i]);
+  return r;
+}
+
+// kLocal: the instance with CTA-local rounds (local_arcs > 0): a bucket of
+// at most blockDim entries whose live entries hold at most local_arcs arcs
+// is expanded by CTA 0 alone, and so are the following buckets while they
+// stay that small, with CTA barriers only; the other CTAs wait at one grid
+// barrier and resume from the bucket state CTA 0 hands back.  A separate
+// instance, so that the other one's registers are those of the rounds alone.
+template <bool kDelta, bool kLocal>
 __global__ void __launch_bounds__(1024) wbfs_kernel(WbfsParams P) {
   extern __shared__ unsigned long long smem_raw[];
   __shared__ int s_flag;
@@ -436,6 +472,7 @@ __global__ void __launch_bounds__(1024) wbfs_kernel(WbfsParams P) {
   const SmemShape sh = wbfs_smem_shape(P.bmax, P.cap, nB);
   PushSmem S = carve_push_smem(smem_raw, sh);
   uint32_t *s_base = (uint32_t *)((char *)smem_raw + push_smem_bytes(sh));
+  uint32_t *s_cnt = s_base + nB;
   for (int i = threadIdx.x; i < nB; i += blockDim.x) s_base[i] = 0u;
   for (int i = threadIdx.x; i < kMaskWords; i += blockDim.x) {
     s_pend[i] = (i == 0) ? 1u : 0u;  // the source sits in slot 0
@@ -474,12 +511,18 @@ __global__ void __launch_bounds__(1024) wbfs_kernel(WbfsParams P) {
   if (P.inject_wait && blockIdx.x == 0 && threadIdx.x == 0) injected_wait(ctl, P.cap_ns);
   __syncthreads();
   bool ok = grid_sync(ctl, bar, &s_flag);
+  // the slot counters after makeBuckets; no round has filed yet
+  RoundState rs = read_round_state(P, 0, s_cnt);
+  rs.mask = 0u;
+  rs.side = 0u;
 
   int32_t lo = 0;
   int bem = 0;         // blocked edgeMap invocations so far
   int cur = 0;         // active overflow buffer
   int32_t prev = -1;   // slot consumed by the previous round (-1: none)
   int32_t bcur = -1;   // Δ-stepping: the bucket being processed
+  bool in_local = false;         // kLocal, CTA 0: inside a run of CTA-local rounds
+  unsigned long long t_loc = 0;  // kLocal, thread 0 of CTA 0: when that run began
   for (int32_t t = 1; ok; t++) {
     // ---------------- nextBucket.  Pending slots: those of the last round
     // minus the one it consumed, plus every slot filed into during it (the
@@ -489,24 +532,97 @@ __global__ void __launch_bounds__(1024) wbfs_kernel(WbfsParams P) {
     if (threadIdx.x < kMaskWords) {
       unsigned pm = s_pend[threadIdx.x];
       if (prev >= 0 && (prev >> 5) == (int)threadIdx.x) pm &= ~(1u << (prev & 31));
-      if (t > 1) pm |= ld_vol(ctl->imask[(t - 1) % 3][threadIdx.x]);
+      pm |= rs.mask;
       s_pend[threadIdx.x] = pm;
       s_pub[threadIdx.x] = 0u;
     }
+    // a run of CTA-local rounds ends after an eighth of the barrier's time
+    // limit, so the CTAs waiting for it never come near that limit
+    if (kLocal && in_local && threadIdx.x == 0)
+      s_int[34] = (long long)(globaltimer() - t_loc) > P.cap_ns / 8 ? 1 : 0;
     __syncthreads();
     if (blockIdx.x == 0 && threadIdx.x < kMaskWords) st_vol(ctl->imask[(t + 1) % 3][threadIdx.x], 0u);
     if (blockIdx.x == 0 && threadIdx.x == 0) st_vol(ctl->fr[(t + 1) % 3], 0ull);
     // Δ-stepping: vertices lowered into the current bucket during round t-1
     // (its side list, complete at the barrier) are expanded again before the
     // bucket is left.  Counter slots by t % 3: this round files into t % 3,
-    // and (t + 1) % 3 was last read at the top of round t - 1.
+    // round t - 1's count was read after its barrier, and (t + 1) % 3 was
+    // last read before round t - 1 began.
     uint32_t side_cnt = 0;
     if (kDelta) {
-      side_cnt = min(ld_vol(ctl->scnt[(t + 2) % 3]), (uint32_t)g.n);
+      side_cnt = min(rs.side, (uint32_t)g.n);
       if (blockIdx.x == 0 && threadIdx.x == 0) st_vol(ctl->scnt[(t + 1) % 3], 0u);
     }
     const bool side_round = kDelta && side_cnt > 0;
     const int32_t b = side_round ? bcur : next_bucket(s_pend, nB, lo, s_int);
+    // ---------------- CTA-local rounds (kLocal, exact wBFS).  Every CTA
+    // loads the bucket's entries and sums their live degrees, so all take
+    // the same decision without a barrier; CTA 0 keeps the loads for its
+    // expansion, thread i's entry in S.u/S.adj/S.base[i] (degree, or ~0 if
+    // not live; bmax >= blockDim).
+    bool pre = false;
+    if constexpr (kLocal && !kDelta) {
+      bool loc = false;
+      if (b != kInf) {
+        const int sb0 = b % nB;
+        const uint32_t rb0 = s_base[sb0], cnt0 = min(s_cnt[sb0] - rb0, (uint32_t)g.n);
+        const bool dense0 = P.dense && P.pull_divisor > 0 &&
+                            (unsigned long long)cnt0 * (unsigned)P.pull_divisor > (unsigned long long)g.n;
+        if (!dense0 && cnt0 <= blockDim.x) {
+          pre = true;
+          uint32_t deg = 0;
+          S.base[threadIdx.x] = ~0u;
+          if (threadIdx.x < cnt0) {
+            const int32_t v = P.slots[(size_t)sb0 * (size_t)g.n + (rb0 + threadIdx.x) % (uint32_t)g.n];
+            const int32_t dv = P.dist[v];
+            const uint32_t o0 = __ldg(g.off + v), o1 = __ldg(g.off + v + 1);
+            deg = o1 - o0;
+            if (dv == b && (deg >= 2u || (deg == 1u && v == src))) {
+              S.u[threadIdx.x] = v;
+              S.adj[threadIdx.x] = o0;
+              S.base[threadIdx.x] = deg;
+            } else {
+              deg = 0;
+            }
+          }
+          uint32_t tot;
+          block_excl_scan(deg, S.misc + 8, &tot);
+          loc = tot <= (uint32_t)P.local_arcs;
+        }
+      }
+      bool wait_local = false;
+      if (in_local && (!loc || s_int[34])) {
+        // CTA 0 ends its run before round t: the state as of this point
+        for (int i = threadIdx.x; i < nB; i += blockDim.x) ctl->loc_base[i] = s_base[i];
+        if (threadIdx.x < kMaskWords) ctl->loc_pend[threadIdx.x] = s_pend[threadIdx.x];
+        if (threadIdx.x == 0) {
+          ctl->loc_t = t;
+          ctl->loc_lo = lo;
+        }
+        in_local = false;
+        wait_local = true;
+      } else if (!in_local && loc) {
+        if (blockIdx.x == 0) {
+          in_local = true;
+          if (threadIdx.x == 0) t_loc = globaltimer();
+        } else {
+          wait_local = true;
+        }
+      }
+      if (wait_local) {
+        if (!grid_sync(ctl, bar, &s_flag)) break;
+        // every CTA resumes at round loc_t from the state CTA 0 handed back
+        t = ld_vol(ctl->loc_t) - 1;
+        lo = ld_vol(ctl->loc_lo);
+        for (int i = threadIdx.x; i < nB; i += blockDim.x) s_base[i] = ld_vol(ctl->loc_base[i]);
+        if (threadIdx.x < kMaskWords) s_pend[threadIdx.x] = ld_vol(ctl->loc_pend[threadIdx.x]);
+        prev = -1;
+        rs = read_round_state(P, t, s_cnt);
+        rs.mask = 0u;
+        rs.side = 0u;
+        continue;
+      }
+    }
     if (b == kInf) {
       // open buckets are dry: refill from the overflow bucket, or finish
       const uint32_t oc = min(ld_vol(ctl->ovf_cnt[cur]), P.ovf_cap);
@@ -534,6 +650,8 @@ __global__ void __launch_bounds__(1024) wbfs_kernel(WbfsParams P) {
       }
       cur ^= 1;
       if (!grid_sync(ctl, bar, &s_flag)) break;
+      // the refill filed into mask t % 3
+      rs = read_round_state(P, t, s_cnt);
       continue;
     }
     // The entries of this round: bucket b's ring slot, or (Δ-stepping) the
@@ -552,7 +670,7 @@ __global__ void __launch_bounds__(1024) wbfs_kernel(WbfsParams P) {
       // above b, less than nB above; Δ-stepping files bucket b into the side
       // list), so its counter is stable here.
       rb = s_base[sb];
-      const uint32_t avail = ld_vol(P.slot_cnt[sb]) - rb;
+      const uint32_t avail = s_cnt[sb] - rb;
       if (avail > (uint32_t)g.n && blockIdx.x == 0 && threadIdx.x == 0)
         raise_error(ctl, GBF_ERR_OVERFLOW, 15);  // a ring wrapped over unconsumed entries
       cntb = min(avail, (uint32_t)g.n);
@@ -564,13 +682,14 @@ __global__ void __launch_bounds__(1024) wbfs_kernel(WbfsParams P) {
     unsigned long long *fctr = &ctl->fr[t % 3];
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&ctl->rounds, 1);
     FileSink fsink{&P, lo, cur, &c, imask, s_pub, kDelta ? b : -1, P.side[t & 1], P.sflag[t & 1],
-                   &ctl->scnt[t % 3]};
+                   &ctl->scnt[t % 3], kLocal && in_local ? s_cnt : nullptr};
     const bool dense = !kDelta && P.dense && P.pull_divisor > 0 &&
                        (unsigned long long)cntb * (unsigned)P.pull_divisor > (unsigned long long)g.n;
     if (dense) {
       if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&ctl->pull_rounds, 1);
       dense_round(P, b, S, fsink, c);
       if (!grid_sync(ctl, bar, &s_flag)) break;
+      rs = read_round_state(P, t, s_cnt);
       if (P.trace && blockIdx.x == 0 && threadIdx.x == 0 && t <= P.trace_cap)
         P.trace[t - 1] = TraceRec{t, 2, cntb, 0u, (long long)(globaltimer() - t_start), 0};
       continue;
@@ -586,21 +705,34 @@ __global__ void __launch_bounds__(1024) wbfs_kernel(WbfsParams P) {
       int32_t v = 0;
       bool live = false;
       uint32_t a0 = 0, deg = 0;
-      if (i < cntb) {
+      if (kLocal && pre && it == 0) {  // CTA 0: the entries the test above loaded
+        const uint32_t d = S.base[threadIdx.x];
+        live = d != ~0u;
+        if (live) {
+          v = S.u[threadIdx.x];
+          a0 = S.adj[threadIdx.x];
+          deg = d;
+        }
+      } else if (i < cntb) {
         v = elist[side_round ? i : (rb + i) % (uint32_t)g.n];
         if (side_round) atomicAnd(P.sflag[(t + 1) & 1] + (v >> 5), ~(1u << (v & 31)));
+        // the entry's distance and its CSR range, loaded together
+        const int32_t dv = P.dist[v];
+        const uint32_t o0 = __ldg(g.off + v), o1 = __ldg(g.off + v + 1);
         // Δ-stepping: a bucket may hold a vertex more than once (lowered
         // twice inside its range before the bucket came up); it is expanded
         // once per round, which also bounds a round's arcs by m
-        if ((P.dist[v] >> P.dl) == b && (!kDelta || atomicExch(P.xround + v, t) != t)) {
-          a0 = __ldg(g.off + v);
-          deg = __ldg(g.off + v + 1) - a0;
+        if ((dv >> P.dl) == b && (!kDelta || atomicExch(P.xround + v, t) != t)) {
+          a0 = o0;
+          deg = o1 - o0;
           // a degree-1 vertex other than the source was reached from its only
           // neighbour, which it cannot improve
           live = deg >= 2u || (deg == 1u && v == src);
         }
       }
-      const bool heavy = live && deg > (uint32_t)P.heavy;
+      // (a CTA-local round expands every entry itself: its arcs fit the
+      // 20-bit degree field below)
+      const bool heavy = !(kLocal && in_local) && live && deg > (uint32_t)P.heavy;
       stage_append(S, heavy, v, deg, a0);
       const bool light = live && !heavy;
       if (live) c.expanded++;
@@ -626,10 +758,26 @@ __global__ void __launch_bounds__(1024) wbfs_kernel(WbfsParams P) {
     }
     stage_flush(S, fout, ctl);
     fsink.flush(S);
+    if (kLocal && in_local) {
+      // the next round starts from this CTA's own filings (complete after
+      // the flush's barriers) and its own slot counters
+      if (threadIdx.x < kMaskWords) rs.mask = s_pub[threadIdx.x];
+      rs.side = 0u;
+      c.relax += fn.relax;
+      if (threadIdx.x == 0) {
+        atomicAdd(&ctl->local_rounds, 1);
+        if (P.trace && t <= P.trace_cap)
+          P.trace[t - 1] = TraceRec{t, 8, cntb, 0u, (long long)(globaltimer() - t_start), 0};
+      }
+      continue;
+    }
     if (!grid_sync(ctl, bar, &s_flag)) break;
     // heavy-vertex counter of this round (triple-buffered: the slot zeroed by
-    // CTA 0 in round t + 1 is (t + 2) % 3, never this one)
+    // CTA 0 in round t + 1 is (t + 2) % 3, never this one), loaded with the
+    // state the next round starts from, which is final here unless a heavy
+    // pass follows
     const unsigned long long fr = ld_vol(*fctr);
+    rs = read_round_state(P, t, s_cnt);
     const uint32_t hcnt = (uint32_t)(fr >> 32), hD = (uint32_t)fr;
     const long long t_mid = (long long)(globaltimer() - t_start);
     if (hcnt > 0 && ((uint64_t)hD + kFine - 1) / kFine > P.cs_cap) {
@@ -646,6 +794,7 @@ __global__ void __launch_bounds__(1024) wbfs_kernel(WbfsParams P) {
       fsink.flush(S);
       if (blockIdx.x == 0 && threadIdx.x == 0) c.scanned += hD;
       if (!grid_sync(ctl, bar, &s_flag)) break;
+      rs = read_round_state(P, t, s_cnt);
     }
     c.relax += fn.relax;
     if (P.trace && blockIdx.x == 0 && threadIdx.x == 0 && t <= P.trace_cap)
@@ -704,6 +853,7 @@ gbf_status launch_wbfs(Graph &g, Workspace &ws, int32_t src, int32_t *dist, cons
   P.log2_bmax_fine = l;
   // vertices with more arcs than this go through the blocked edgeMap pass
   P.heavy = o.heavy_cutoff / 8 > 32 ? o.heavy_cutoff / 8 : 32;
+  P.local_arcs = dl == 0 ? o.local_arcs : 0;
   P.inject_wait = o.inject_wait;
   P.cap_ns = o.spin_cap_ns;
   P.dl = dl;
@@ -712,9 +862,10 @@ gbf_status launch_wbfs(Graph &g, Workspace &ws, int32_t src, int32_t *dist, cons
   P.sflag[0] = ws.fbm[0];
   P.sflag[1] = ws.fbm[1];
   P.xround = ws.xround;
-  const void *kern = dl > 0 ? (const void *)wbfs_kernel<true> : (const void *)wbfs_kernel<false>;
-  const size_t smem =
-      push_smem_bytes(wbfs_smem_shape(P.bmax, P.cap, ws.nB)) + sizeof(uint32_t) * (size_t)ws.nB;
+  const void *kern = dl > 0 ? (const void *)wbfs_kernel<true, false>
+                            : (P.local_arcs > 0 ? (const void *)wbfs_kernel<false, true>
+                                                : (const void *)wbfs_kernel<false, false>);
+  const size_t smem = wbfs_smem_bytes(P.bmax, P.cap, ws.nB);
   {
     const gbf_status sm = check_smem(smem, "wbfs_kernel");
     if (sm != GBF_OK) return sm;
@@ -739,13 +890,12 @@ gbf_status launch_wbfs(Graph &g, Workspace &ws, int32_t src, int32_t *dist, cons
 }
 
 int resident_ctas_per_sm_wbfs(const Opts &o, int nB) {
-  const size_t smem = push_smem_bytes(wbfs_smem_shape(o.heavy_cutoff, stage_capacity(o.block), nB)) +
-                      sizeof(uint32_t) * (size_t)nB;
-  if (cudaFuncSetAttribute(wbfs_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const size_t smem = wbfs_smem_bytes(o.heavy_cutoff, stage_capacity(o.block), nB);
+  if (cudaFuncSetAttribute(wbfs_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)smem) != cudaSuccess)
     return 0;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wbfs_kernel<false>, o.block, smem) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, wbfs_kernel<false, false>, o.block, smem) !=
       cudaSuccess)
     return 0;
   return per_sm;

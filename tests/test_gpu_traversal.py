@@ -187,6 +187,29 @@ def test_wbfs_grid(gb):
     _wbfs_parity(gb, csr, [0, 9000], opts=(None, gb.gbf_options_default(bucket_window=4)))
 
 
+def test_wbfs_cta_local_rounds(gb):
+    """With local_arcs set, small buckets are expanded by one CTA alone
+    (local_rounds > 0); the distances equal Dijkstra's with the mode off (the
+    default), with an arc limit so small that runs start and stop every few
+    rounds, and with the largest limit, on a graph of few hubs and on a
+    high-diameter grid."""
+    for csr in (G.add_weights(G.rmat(14, 16, seed=61), 1, 22, seed=62),
+                G.add_weights(G.grid(120, 130, 0.1, seed=63), 1, 16, seed=64)):
+        g = gb.Graph(csr)
+        for s in G.sources(csr, 2, seed=65):
+            ref = oracle.dijkstra(csr, int(s))
+            local = {}
+            for la in (0, -1, 3, 4096, (1 << 20) - 1):
+                d = g.wbfs(int(s), opt=gb.gbf_options_default(local_arcs=la))
+                st = g.stats()
+                assert np.array_equal(d, ref), (csr.name, int(s), la)
+                assert st["device_error"] == 0
+                local[la] = st["local_rounds"]
+            assert local[0] == 0 and local[-1] == 0, (csr.name, local)
+            assert local[4096] > 0 and local[(1 << 20) - 1] > 0, (csr.name, local)
+        g.close()
+
+
 def test_wbfs_tiny_many(gb):
     for s in range(40):
         csr = G.random_small(2 + (s % 60), [0.05, 0.15, 0.4][s % 3], 100 + s, w_hi=[2, 9, 30][s % 3])
@@ -281,6 +304,13 @@ def test_round_trace(gb):
     g.wbfs(s)
     tr = gb.gbf_trace(g.h)
     assert len(tr) == g.stats()["rounds"] > 0
+    assert {r[1] for r in tr} <= {1, 2, 3}
+    g.wbfs(s, opt=gb.gbf_options_default(local_arcs=4096))
+    tr = gb.gbf_trace(g.h)
+    assert len(tr) == g.stats()["rounds"] > 0
+    assert [r[0] for r in tr] == list(range(1, len(tr) + 1))
+    assert {r[1] for r in tr} <= {1, 2, 3, 8}
+    assert sum(r[1] == 8 for r in tr) == g.stats()["local_rounds"] > 0
 
 
 def test_sparse_graphs_default_to_half_the_sms(gb):
