@@ -339,12 +339,13 @@ def bytes_model(kind, n, st):
         # writeMin/Max: the atomic and the flag test-and-set (8)
         return 4 * n + n // 4 + 16 * V + 16 * E + 8 * R
     if kind == "mssp":
-        # init and final read of the 8 distance lanes (2 x 32n), every row
-        # written once (4kn, k = 8); per scanned arc: target, weight and the
-        # target's 32-byte lane sector (40); per frontier vertex: queue entry,
-        # prefix, first arc and its lane byte (16); per successful writeMin:
-        # the atomic and the lane-mask OR (8)
-        return 64 * n + 32 * n + 40 * E + 16 * V + 8 * R
+        # 16-bit lanes (the bench's graphs never need the 32-bit rerun: their
+        # distances stay far below 65,535): init and final read of the 8
+        # distance lanes (2 x 16n), every row written once (4kn, k = 8); per
+        # scanned arc: target, weight and the target's 16-byte lane word (24);
+        # per frontier vertex: queue entry, prefix, first arc and its lane
+        # byte (16); per successful lowering: the swap and the lane-mask OR (8)
+        return 32 * n + 32 * n + 24 * E + 16 * V + 8 * R
     if kind == "msbfs":
         # init seen/visit/next (32n); every dist[i][v] written once (4kn); per
         # scanned arc: target + the neighbour's lane word (12); per frontier

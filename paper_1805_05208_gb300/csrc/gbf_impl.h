@@ -52,6 +52,7 @@ struct Ctl {
   unsigned long long heavy;
   unsigned long long pulled;   // dense-round candidates
   int rounds, push_rounds, pull_rounds, refills, local_rounds;
+  unsigned int lane_ovf;       // multi-source SSSP: a 16-bit lane could not hold a distance
   // wBFS: bucket state CTA 0 hands back after a run of CTA-local rounds
   int loc_t, loc_lo;
   unsigned int loc_pend[8];

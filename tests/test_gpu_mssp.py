@@ -111,3 +111,32 @@ def test_mssp_device_buffers_and_errors(gb):
     with pytest.raises(gb.GbfError):
         unweighted.mssp([0])
     unweighted.close()
+
+
+def test_mssp_lane_width_limit_and_fallback(gb):
+    """A query first runs with 16-bit lanes, which hold distances up to
+    65,534.  A distance of 65,534 is exact in them; one of 65,535 does not
+    fit, and the launch reruns the query with 32-bit lanes, bit-exact all the
+    same, as are later calls on that graph (which start with 32-bit lanes).
+    Lanes with near and far sources share one launch."""
+    for wt, srcs in ((65534, [0, 1]), (65535, [0, 1]), (65536, [1, 0, 1])):
+        csr = G.csr_from_edges(3, [(0, 1)], [wt])
+        g = gb.Graph(csr)
+        for rep in range(3):
+            d = g.mssp(srcs)
+            for i, s in enumerate(srcs):
+                ref = oracle.dijkstra(csr, int(s))
+                assert np.array_equal(d[i], ref), (wt, rep, i, d[i], ref)
+        g.close()
+    n = 300
+    w = np.full(n - 1, 500, dtype=np.int64)     # distances up to 149,500
+    path = G.path_graph(n, weights=w)
+    pre = np.concatenate([[0], np.cumsum(w)])
+    g = gb.Graph(path)
+    srcs = [0, 150, 299, 10, 149]
+    for rep in range(3):
+        d = g.mssp(srcs)
+        for i, s in enumerate(srcs):
+            assert np.array_equal(d[i], np.abs(pre - pre[s])), (rep, i)
+    assert g.stats()["device_error"] == 0
+    g.close()
