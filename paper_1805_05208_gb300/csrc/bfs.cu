@@ -406,7 +406,9 @@ __device__ void pull_level(const BfsParams &P, PushSmem &S, const uint32_t *fin,
     // ring, then start loading the next group
     if (have && tail - head < kRing - 32 * kGroupWords - 32) {
       bool cd[kGroupWords];
-      uint32_t za[kGroupWords], fw[kGroupWords];
+      uint32_t za[kGroupWords];
+      unsigned cb[kGroupWords];
+      uint32_t ncand = 0;
 #pragma unroll
       for (uint32_t r = 0; r < kGroupWords; r++) {
         const uint32_t vis = __shfl_sync(kFull, pvis, r);
@@ -418,24 +420,49 @@ __device__ void pull_level(const BfsParams &P, PushSmem &S, const uint32_t *fin,
         const uint32_t v = (pw + r) * 32 + lane;
         cd[r] = v < (uint32_t)g.n && !((vis >> lane) & 1u) && z > a;
         za[r] = z;
-        fw[r] = (f1 && cd[r]) ? fin[(uint32_t)ph[r] >> 5] : 0u;
+        cb[r] = __ballot_sync(kFull, cd[r]);
+        ncand += __popc(cb[r]);
       }
+      if (f1 && ncand <= 32) {
+        // a sparse group: its candidates side by side, one per lane (lane j
+        // takes the j-th, found in its word's ballot), so the first-arc
+        // checks, the records and the ring appends run once for all words
+        const uint32_t c0 = __popc(cb[0]), c1 = c0 + __popc(cb[1]), c2 = c1 + __popc(cb[2]);
+        const uint32_t j = (uint32_t)lane;
+        const bool act = j < ncand;
+        const uint32_t r = (j >= c0 ? 1u : 0u) + (j >= c1 ? 1u : 0u) + (j >= c2 ? 1u : 0u);
+        const uint32_t nth = j - (r == 0 ? 0u : r == 1 ? c0 : r == 2 ? c1 : c2);
+        const unsigned br = r == 0 ? cb[0] : r == 1 ? cb[1] : r == 2 ? cb[2] : cb[3];
+        const int own = act ? (int)__fns(br, 0u, (int)nth + 1) : 0;  // the candidate's lane
+        uint32_t a = 0, z = 0;
+        int32_t h = -1;
 #pragma unroll
-      for (uint32_t r = 0; r < kGroupWords; r++) {
-        const uint32_t a = pa[r], z = za[r];
-        const uint32_t v = (pw + r) * 32 + lane;
-        const bool hit = f1 && cd[r] && ((fw[r] >> (ph[r] & 31)) & 1u);
-        if (cd[r]) {
+        for (uint32_t q = 0; q < kGroupWords; q++) {
+          const uint32_t xa = __shfl_sync(kFull, pa[q], own), xz = __shfl_sync(kFull, za[q], own);
+          const int32_t xh = __shfl_sync(kFull, ph[q], own);
+          if (q == r) {
+            a = xa;
+            z = xz;
+            h = xh;
+          }
+        }
+        const uint32_t v = (pw + r) * 32 + (uint32_t)own;
+        const uint32_t fwv = act ? fin[(uint32_t)h >> 5] : 0u;
+        const bool hit = act && ((fwv >> (h & 31)) & 1u);
+        if (act) {
           cand_cnt++;
           C.scanned += skip;
         }
-        const unsigned hb = __ballot_sync(kFull, hit);
-        if (hit) C.record(P, (int32_t)v, ph[r], z - a);
-        if (hb && lane == 0) {
-          atomicOr(fout + pw + r, hb);
-          atomicOr(P.visited + pw + r, hb);
+        if (hit) C.record(P, (int32_t)v, h, z - a);
+#pragma unroll
+        for (uint32_t q = 0; q < kGroupWords; q++) {
+          const unsigned hb = __reduce_or_sync(kFull, (hit && r == q) ? 1u << own : 0u);
+          if (hb && lane == (int)q) {
+            atomicOr(fout + pw + q, hb);
+            atomicOr(P.visited + pw + q, hb);
+          }
         }
-        const bool c = cd[r] && !hit && z - a > skip;
+        const bool c = act && !hit && z - a > skip;
         const unsigned bal = __ballot_sync(kFull, c);
         if (c) {
           const uint32_t i = (tail + __popc(bal & lt)) & (kRing - 1);
@@ -444,6 +471,36 @@ __device__ void pull_level(const BfsParams &P, PushSmem &S, const uint32_t *fin,
           re[i] = z;
         }
         tail += __popc(bal);
+      } else {
+        uint32_t fw[kGroupWords];
+#pragma unroll
+        for (uint32_t r = 0; r < kGroupWords; r++)
+          fw[r] = (f1 && cd[r]) ? fin[(uint32_t)ph[r] >> 5] : 0u;
+#pragma unroll
+        for (uint32_t r = 0; r < kGroupWords; r++) {
+          const uint32_t a = pa[r], z = za[r];
+          const uint32_t v = (pw + r) * 32 + lane;
+          const bool hit = f1 && cd[r] && ((fw[r] >> (ph[r] & 31)) & 1u);
+          if (cd[r]) {
+            cand_cnt++;
+            C.scanned += skip;
+          }
+          const unsigned hb = __ballot_sync(kFull, hit);
+          if (hit) C.record(P, (int32_t)v, ph[r], z - a);
+          if (hb && lane == 0) {
+            atomicOr(fout + pw + r, hb);
+            atomicOr(P.visited + pw + r, hb);
+          }
+          const bool c = cd[r] && !hit && z - a > skip;
+          const unsigned bal = __ballot_sync(kFull, c);
+          if (c) {
+            const uint32_t i = (tail + __popc(bal & lt)) & (kRing - 1);
+            rv[i] = (int32_t)v;
+            rs[i] = a;
+            re[i] = z;
+          }
+          tail += __popc(bal);
+        }
       }
       have = false;
       __syncwarp();
