@@ -204,6 +204,8 @@ struct MsspFn {
         if (prev[j] == cur[j]) {
           const uint32_t lt = __vcmpltu2(nw[j], cur[j]);
           better |= ((lt & 1u) << (2 * j)) | (((lt >> 16) & 1u) << (2 * j + 1));
+        } else {
+          raise_error(ctl, GBF_ERR_TIMEOUT, 21);  // the cap: never expected
         }
       }
       return better;
