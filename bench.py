@@ -91,6 +91,9 @@ WORKLOADS = {
     "mssp-rmat20": dict(kind="mssp", graph="rmat", scale=20, ef=16, w=(1, 22), nsrc=8,
                         desc="multi-source SSSP, 8 sources in one launch, RMAT scale 20 ef16, "
                              "w in [1,22)"),
+    "mssp-rmat24": dict(kind="mssp", graph="rmat", scale=24, ef=16, w=(1, 22), nsrc=8,
+                        desc="multi-source SSSP, 8 sources in one launch, RMAT scale 24 ef16, "
+                             "w in [1,22) (the serving mix's largest graph)"),
     "serve": dict(kind="serve", graph="rmat", scales=(18, 20, 22, 24), ef=16, w=(1, 22), nsrc=0,
                   rates=(1000, 2000, 5000, 10000, 20000, 50000), warm=2000, meas=20000,
                   desc="serving: 4 resident RMAT graphs (scales 18/20/22/24, ef16, w in [1,22)), "
