@@ -190,6 +190,24 @@ gbf_status gbf_bfs(gbf_graph *g, int32_t src, int32_t *dist, int32_t *parent, in
                    const gbf_options *opt, void *cuda_stream);
 
 /*
+ * gbf_bfs_host_batch — k BFS queries of gbf_bfs (§4 "Breadth-First Search";
+ * Alg. 1) with their results in host memory, each query's read-back
+ * overlapping the next query's search: the results go to two device buffers
+ * in turn, and a second stream copies one out while the next query runs.
+ *   srcs    int32[k] host array of sources, k >= 1
+ *   dist    host int32[k * n]: row i = the distances from srcs[i]
+ *   parent  host int32[k * n] or NULL: row i = a BFS tree of srcs[i]
+ *   opt     NULL for defaults
+ * Blocks until every row is in host memory; page-locked (pinned) buffers
+ * let the copies overlap the searches.  Returns the first device status of
+ * the batch.  Allocates a second result buffer pair and a copy stream on the
+ * graph's first call.  gbf_wait afterwards reports the last query.
+ * Errors: GBF_ERR_INVALID for k < 1, a bad source or NULL srcs/dist.
+ */
+gbf_status gbf_bfs_host_batch(gbf_graph *g, const int32_t *srcs, int32_t k, int32_t *dist,
+                              int32_t *parent, const gbf_options *opt, void *cuda_stream);
+
+/*
  * gbf_wbfs — integral-weight single-source shortest paths from src by
  * weighted BFS over a Julienne bucket structure (§4 "Integral-Weight SSSP";
  * Alg. 3).  Requires a weighted graph with weights >= 1.

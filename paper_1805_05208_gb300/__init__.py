@@ -101,6 +101,7 @@ def _load() -> ctypes.CDLL:
                                ctypes.POINTER(U64)]),
         "gbf_graph_device_bytes": (S, [P, ctypes.POINTER(ctypes.c_size_t)]),
         "gbf_bfs": (S, [P, I32, P, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
+        "gbf_bfs_host_batch": (S, [P, P, I32, P, P, ctypes.POINTER(gbf_options), P]),
         "gbf_wbfs": (S, [P, I32, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
         "gbf_delta_stepping": (S, [P, I32, I32, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
         "gbf_ldd": (S, [P, P, P, P, ctypes.c_int, ctypes.POINTER(gbf_options), P]),
@@ -224,6 +225,29 @@ def gbf_bfs(h: int, src: int, dist, parent=None, opt: Optional[gbf_options] = No
     if mp is not None and mp != mem:
         raise ValueError("dist and parent must live in the same memory")
     _check(_lib.gbf_bfs(h, int(src), pd, pp, mem, _opt(opt), _stream(stream)), "gbf_bfs")
+
+
+def _check_host_rows(name, a, k, n):
+    """A C-contiguous host int32 array of k rows of n entries."""
+    if not isinstance(a, np.ndarray) or a.dtype != np.int32 or not a.flags["C_CONTIGUOUS"]:
+        raise ValueError(f"gbf_bfs_host_batch: {name} must be a contiguous int32 numpy array")
+    if a.size != k * n:
+        raise ValueError(f"gbf_bfs_host_batch: {name} holds {a.size} entries, needs {k} x {n}")
+
+
+def gbf_bfs_host_batch(h: int, srcs, dist, parent=None, opt: Optional[gbf_options] = None,
+                       stream=None) -> None:
+    """BFS from each source into host rows dist[i] (and parent[i]), blocking;
+    each row's read-back overlaps the next query (pinned arrays, e.g. from
+    torch's pin_memory, let the copies run in the background)."""
+    s = np.ascontiguousarray(np.asarray(srcs, dtype=np.int32))
+    n = gbf_graph_info(h)["n"]
+    _check_host_rows("dist", dist, int(s.size), n)
+    if parent is not None:
+        _check_host_rows("parent", parent, int(s.size), n)
+    _check(_lib.gbf_bfs_host_batch(h, s.ctypes.data, int(s.size), dist.ctypes.data,
+                                   None if parent is None else parent.ctypes.data, _opt(opt),
+                                   _stream(stream)), "gbf_bfs_host_batch")
 
 
 def gbf_wbfs(h: int, src: int, dist, opt: Optional[gbf_options] = None, stream=None) -> None:

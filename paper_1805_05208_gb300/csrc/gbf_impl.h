@@ -97,6 +97,14 @@ struct Workspace {
   Ctl *ctl = nullptr;
   int32_t *dist_tmp = nullptr;     // used for host-memory outputs
   int32_t *parent_tmp = nullptr;
+  // batched BFS to host memory (lazy): a second result buffer pair, the
+  // read-back stream, its events, and the first device status of the batch
+  int32_t *dist_tmp2 = nullptr;
+  int32_t *parent_tmp2 = nullptr;
+  cudaStream_t hb_stream = nullptr;
+  cudaEvent_t hb_kern_done[2] = {nullptr, nullptr}, hb_copy_done[2] = {nullptr, nullptr};
+  int *hb_err = nullptr;
+  int *hb_err_host = nullptr;
   TraceRec *trace = nullptr;
   int trace_cap = 0;
   // wBFS (lazy)

@@ -246,6 +246,11 @@ gbf_status dmalloc(T **p, size_t count, size_t &acc) {
     if (_s != GBF_OK) return _s;        \
   } while (0)
 
+// The first nonzero device status of a batch of launches.
+__global__ void k_keep_error(int *acc, const int *err) {
+  if (*acc == 0) *acc = *err;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------- workspaces
@@ -381,7 +386,7 @@ void ws_free(Workspace &ws) {
                   ws.ms_q[2], ws.ms_qoff[2], ws.ms_cs[2], ws.ms_touched, ws.ms_call,
                   ws.ms_dist_tmp, ws.bc_paths, ws.bc_lvl, ws.bc_cs, ws.bc_info,
                   ws.bc_out_tmp, ws.side[0], ws.side[1], ws.xround, ws.mssp_dd, ws.mssp_imp,
-                  ws.mssp_out_tmp};
+                  ws.mssp_out_tmp, ws.dist_tmp2, ws.parent_tmp2, ws.hb_err};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (ws.ctl_host) cudaFreeHost(ws.ctl_host);
@@ -390,6 +395,12 @@ void ws_free(Workspace &ws) {
   if (ws.ms_ready) cudaEventDestroy(ws.ms_ready);
   if (ws.ms_done) cudaEventDestroy(ws.ms_done);
   if (ws.ms_stream) cudaStreamDestroy(ws.ms_stream);
+  if (ws.hb_err_host) cudaFreeHost(ws.hb_err_host);
+  for (int i = 0; i < 2; i++) {
+    if (ws.hb_kern_done[i]) cudaEventDestroy(ws.hb_kern_done[i]);
+    if (ws.hb_copy_done[i]) cudaEventDestroy(ws.hb_copy_done[i]);
+  }
+  if (ws.hb_stream) cudaStreamDestroy(ws.hb_stream);
   ws = Workspace();
 }
 
@@ -608,6 +619,64 @@ gbf_status gbf_bfs(gbf_graph *h, int32_t src, int32_t *dist, int32_t *parent, in
   if (parent)
     GBF_CUDA(cudaMemcpyAsync(parent, pp, sizeof(int32_t) * (size_t)g.n, cudaMemcpyDeviceToHost, st));
   return ws_collect(g.ws, st, nullptr);
+}
+
+gbf_status gbf_bfs_host_batch(gbf_graph *h, const int32_t *srcs, int32_t k, int32_t *dist,
+                              int32_t *parent, const gbf_options *opt, void *cuda_stream) {
+  if (!h || !srcs || !dist) return set_error("graph, srcs or dist is NULL"), GBF_ERR_INVALID;
+  Graph &g = h->g;
+  if (k < 1) return set_error("k must be at least 1"), GBF_ERR_INVALID;
+  for (int32_t i = 0; i < k; i++)
+    if (srcs[i] < 0 || srcs[i] >= g.n) return set_error("source out of range"), GBF_ERR_INVALID;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  std::lock_guard<std::mutex> lk(g.mu);
+  GBF_TRY(ws_ensure_base(g, g.ws));
+  Workspace &ws = g.ws;
+  const size_t n = (size_t)g.n;
+  if (!ws.dist_tmp2) {
+    size_t acc = 0;
+    GBF_TRY(dmalloc(&ws.dist_tmp2, n, acc));
+    GBF_TRY(dmalloc(&ws.parent_tmp2, n, acc));
+    GBF_TRY(dmalloc(&ws.hb_err, 1, acc));
+    GBF_CUDA(cudaMallocHost((void **)&ws.hb_err_host, sizeof(int)));
+    GBF_CUDA(cudaStreamCreateWithFlags(&ws.hb_stream, cudaStreamNonBlocking));
+    for (int i = 0; i < 2; i++) {
+      GBF_CUDA(cudaEventCreateWithFlags(&ws.hb_kern_done[i], cudaEventDisableTiming));
+      GBF_CUDA(cudaEventCreateWithFlags(&ws.hb_copy_done[i], cudaEventDisableTiming));
+    }
+    ws.bytes += acc;
+  }
+  const Opts o = resolve(opt, g, GBF_TUNE_BFS);
+  int32_t *dbuf[2] = {ws.dist_tmp, ws.dist_tmp2}, *pbuf[2] = {ws.parent_tmp, ws.parent_tmp2};
+  GBF_CUDA(cudaMemsetAsync(ws.hb_err, 0, sizeof(int), st));
+  for (int b = 0; b < 2; b++) GBF_CUDA(cudaEventRecord(ws.hb_copy_done[b], st));
+  for (int32_t i = 0; i < k; i++) {
+    const int b = i & 1;
+    // result buffer b is free once the read-back of query i - 2 is done
+    GBF_CUDA(cudaStreamWaitEvent(st, ws.hb_copy_done[b], 0));
+    GBF_TRY(launch_bfs(g, ws, srcs[i], dbuf[b], parent ? pbuf[b] : nullptr, o, st));
+    // the query's device status, kept past the next launch's reset of the control block
+    k_keep_error<<<1, 1, 0, st>>>(ws.hb_err, &ws.ctl->err);
+    GBF_CUDA(cudaGetLastError());
+    GBF_CUDA(cudaEventRecord(ws.hb_kern_done[b], st));
+    // read-back on the second stream, while the next query computes
+    GBF_CUDA(cudaStreamWaitEvent(ws.hb_stream, ws.hb_kern_done[b], 0));
+    GBF_CUDA(cudaMemcpyAsync(dist + (size_t)i * n, dbuf[b], sizeof(int32_t) * n,
+                             cudaMemcpyDeviceToHost, ws.hb_stream));
+    if (parent)
+      GBF_CUDA(cudaMemcpyAsync(parent + (size_t)i * n, pbuf[b], sizeof(int32_t) * n,
+                               cudaMemcpyDeviceToHost, ws.hb_stream));
+    GBF_CUDA(cudaEventRecord(ws.hb_copy_done[b], ws.hb_stream));
+  }
+  for (int b = 0; b < 2; b++) GBF_CUDA(cudaStreamWaitEvent(st, ws.hb_copy_done[b], 0));
+  GBF_CUDA(cudaMemcpyAsync(ws.hb_err_host, ws.hb_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  const gbf_status s = ws_collect(ws, st, nullptr);  // synchronises st
+  if (s != GBF_OK) return s;
+  if (*ws.hb_err_host != 0) {
+    set_error("a query of the batch reported a device error");
+    return (gbf_status)*ws.hb_err_host;
+  }
+  return GBF_OK;
 }
 
 gbf_status gbf_wbfs(gbf_graph *h, int32_t src, int32_t *dist, int mem, const gbf_options *opt,

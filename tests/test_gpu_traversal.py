@@ -129,6 +129,39 @@ def test_bfs_repeated_block1024_conversions(gb):
     g.close()
 
 
+def test_bfs_host_batch_matches_single_queries(gb):
+    """gbf_bfs_host_batch (each query's read-back running while the next one
+    searches, two device result buffers in turn) gives every row as gbf_bfs
+    does, for 1, 2, 3 and 5 sources, with and without parents, into pinned
+    and pageable host memory; bad arguments are refused."""
+    torch = pytest.importorskip("torch")
+    csr = G.rmat(14, 16, seed=81)
+    g = gb.Graph(csr, validate=gb.VALIDATE_BASIC | gb.VALIDATE_SYMMETRIC)
+    srcs = G.sources(csr, 5, seed=82)
+    refs = [oracle.bfs(csr, int(s), parents=False)[0] for s in srcs]
+    for k in (1, 2, 3, 5):
+        for pinned in (True, False):
+            def rows():
+                if pinned:
+                    return torch.empty((k, csr.n), dtype=torch.int32, pin_memory=True).numpy()
+                return np.empty((k, csr.n), dtype=np.int32)
+            d, p = rows(), rows()
+            gb.gbf_bfs_host_batch(g.h, srcs[:k], d, p)
+            for i in range(k):
+                assert np.array_equal(d[i], refs[i]), (k, pinned, i)
+                ok, v, why = oracle.check_bfs(csr, int(srcs[i]), d[i], p[i])
+                assert ok, (k, pinned, i, v, why)
+            d2 = rows()
+            gb.gbf_bfs_host_batch(g.h, srcs[:k], d2)
+            assert np.array_equal(d2, d)
+    with pytest.raises(ValueError):
+        gb.gbf_bfs_host_batch(g.h, srcs[:2], np.empty((1, csr.n), dtype=np.int32))
+    with pytest.raises(gb.GbfError):
+        gb.gbf_bfs_host_batch(g.h, np.array([csr.n], dtype=np.int32),
+                              np.empty((1, csr.n), dtype=np.int32))
+    g.close()
+
+
 def test_bfs_grid_deleted_edges(gb):
     csr = G.grid(200, 300, 0.1, seed=7)
     _bfs_parity(gb, csr, [0, 123, 59999], opts=(None, gb.gbf_options_default(ctas=3)))
