@@ -230,15 +230,15 @@ class ClockSampler:
 
 
 KERNEL_SOURCES = {
-    "bfs_kernel": ("bfs.cu", "dev_common.cuh", "gbf_impl.h"),
-    "wbfs_kernel": ("wbfs.cu", "dev_common.cuh", "gbf_impl.h"),
-    "msbfs_kernel": ("msbfs.cu", "dev_common.cuh", "gbf_impl.h"),
-    "bf_kernel": ("bellman_ford.cu", "dev_common.cuh", "gbf_impl.h"),
-    "bc_kernel": ("betweenness.cu", "dev_common.cuh", "gbf_impl.h"),
-    "kcore_kernel": ("kcore.cu", "dev_common.cuh", "gbf_impl.h"),
-    "mssp_kernel": ("mssp.cu", "dev_common.cuh", "gbf_impl.h"),
-    "ldd_kernel": ("ldd.cu", "dev_common.cuh", "gbf_impl.h"),
-    "cc_kernel": ("connectivity.cu", "dev_common.cuh", "gbf_impl.h"),
+    "bfs_kernel": ("bfs.cu", "dev_common.cuh", "gbf_dev.h"),
+    "wbfs_kernel": ("wbfs.cu", "dev_common.cuh", "gbf_dev.h"),
+    "msbfs_kernel": ("msbfs.cu", "dev_common.cuh", "gbf_dev.h"),
+    "bf_kernel": ("bellman_ford.cu", "dev_common.cuh", "gbf_dev.h"),
+    "bc_kernel": ("betweenness.cu", "dev_common.cuh", "gbf_dev.h"),
+    "kcore_kernel": ("kcore.cu", "dev_common.cuh", "gbf_dev.h"),
+    "mssp_kernel": ("mssp.cu", "dev_common.cuh", "gbf_dev.h"),
+    "ldd_kernel": ("ldd.cu", "dev_common.cuh", "gbf_dev.h"),
+    "cc_kernel": ("connectivity.cu", "dev_common.cuh", "gbf_dev.h"),
 }
 
 

@@ -13,7 +13,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "gbf_impl.h"
+#include "../../include/gbf.h"
+#include "gbf_dev.h"
 
 namespace gbf {
 namespace dev {
