@@ -787,6 +787,7 @@ def run_msbfs(args, wl, g, srcs, graph, opt, stream, dev, rank, world, barrier, 
     # end to end: host output buffer, the 64 x n result copied back each step
     host = torch.empty((k, n), dtype=torch.int32, pin_memory=True).numpy()
     e2e_steps = max(1, min(args.steps, 3))
+    gb.gbf_msbfs(graph.h, srcs, host, opt, None)  # untimed warm-up (first-call host-output buffer)
     torch.cuda.synchronize()
     barrier()
     tt0 = time.perf_counter()
@@ -916,6 +917,7 @@ def run_mssp(args, wl, g, srcs, graph, opt, stream, dev, rank, world, barrier, d
     bpl = bytes_model("mssp", n, stats)
     host = torch.empty((k, n), dtype=torch.int32, pin_memory=True).numpy()
     e2e_steps = max(1, min(args.steps, 3))
+    gb.gbf_mssp(graph.h, srcs, host, opt, None)  # untimed warm-up (first-call host-output buffer)
     torch.cuda.synchronize()
     barrier()
     tt0 = time.perf_counter()
@@ -1123,7 +1125,11 @@ def main():
     torch.cuda.synchronize()
     barrier()
     t0 = time.perf_counter()
-    for s in range(e2e_steps):
+    for s in range(-1, e2e_steps):
+        if s == 0:  # step -1 is an untimed warm-up (first-call buffers, copy stream)
+            torch.cuda.synchronize()
+            barrier()
+            t0 = time.perf_counter()
         if kind == "bfs":
             gb.gbf_bfs_host_batch(graph.h, srcs_np, host_d2, host_p2, opt, None)
             continue
