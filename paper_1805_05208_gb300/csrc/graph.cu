@@ -648,25 +648,36 @@ gbf_status gbf_bfs_host_batch(gbf_graph *h, const int32_t *srcs, int32_t k, int3
   }
   const Opts o = resolve(opt, g, GBF_TUNE_BFS);
   int32_t *dbuf[2] = {ws.dist_tmp, ws.dist_tmp2}, *pbuf[2] = {ws.parent_tmp, ws.parent_tmp2};
-  GBF_CUDA(cudaMemsetAsync(ws.hb_err, 0, sizeof(int), st));
-  for (int b = 0; b < 2; b++) GBF_CUDA(cudaEventRecord(ws.hb_copy_done[b], st));
-  for (int32_t i = 0; i < k; i++) {
-    const int b = i & 1;
-    // result buffer b is free once the read-back of query i - 2 is done
-    GBF_CUDA(cudaStreamWaitEvent(st, ws.hb_copy_done[b], 0));
-    GBF_TRY(launch_bfs(g, ws, srcs[i], dbuf[b], parent ? pbuf[b] : nullptr, o, st));
-    // the query's device status, kept past the next launch's reset of the control block
-    k_keep_error<<<1, 1, 0, st>>>(ws.hb_err, &ws.ctl->err);
-    GBF_CUDA(cudaGetLastError());
-    GBF_CUDA(cudaEventRecord(ws.hb_kern_done[b], st));
-    // read-back on the second stream, while the next query computes
-    GBF_CUDA(cudaStreamWaitEvent(ws.hb_stream, ws.hb_kern_done[b], 0));
-    GBF_CUDA(cudaMemcpyAsync(dist + (size_t)i * n, dbuf[b], sizeof(int32_t) * n,
-                             cudaMemcpyDeviceToHost, ws.hb_stream));
-    if (parent)
-      GBF_CUDA(cudaMemcpyAsync(parent + (size_t)i * n, pbuf[b], sizeof(int32_t) * n,
+  // enqueue every query; on a failure, wait for the copies already issued,
+  // so that none writes into the caller's buffers after this call returns
+  auto enqueue = [&]() -> gbf_status {
+    GBF_CUDA(cudaMemsetAsync(ws.hb_err, 0, sizeof(int), st));
+    for (int b = 0; b < 2; b++) GBF_CUDA(cudaEventRecord(ws.hb_copy_done[b], st));
+    for (int32_t i = 0; i < k; i++) {
+      const int b = i & 1;
+      // result buffer b is free once the read-back of query i - 2 is done
+      GBF_CUDA(cudaStreamWaitEvent(st, ws.hb_copy_done[b], 0));
+      GBF_TRY(launch_bfs(g, ws, srcs[i], dbuf[b], parent ? pbuf[b] : nullptr, o, st));
+      // the query's device status, kept past the next launch's reset of the control block
+      k_keep_error<<<1, 1, 0, st>>>(ws.hb_err, &ws.ctl->err);
+      GBF_CUDA(cudaGetLastError());
+      GBF_CUDA(cudaEventRecord(ws.hb_kern_done[b], st));
+      // read-back on the second stream, while the next query computes
+      GBF_CUDA(cudaStreamWaitEvent(ws.hb_stream, ws.hb_kern_done[b], 0));
+      GBF_CUDA(cudaMemcpyAsync(dist + (size_t)i * n, dbuf[b], sizeof(int32_t) * n,
                                cudaMemcpyDeviceToHost, ws.hb_stream));
-    GBF_CUDA(cudaEventRecord(ws.hb_copy_done[b], ws.hb_stream));
+      if (parent)
+        GBF_CUDA(cudaMemcpyAsync(parent + (size_t)i * n, pbuf[b], sizeof(int32_t) * n,
+                                 cudaMemcpyDeviceToHost, ws.hb_stream));
+      GBF_CUDA(cudaEventRecord(ws.hb_copy_done[b], ws.hb_stream));
+    }
+    return GBF_OK;
+  };
+  const gbf_status es = enqueue();
+  if (es != GBF_OK) {
+    cudaStreamSynchronize(ws.hb_stream);
+    cudaStreamSynchronize(st);
+    return es;
   }
   for (int b = 0; b < 2; b++) GBF_CUDA(cudaStreamWaitEvent(st, ws.hb_copy_done[b], 0));
   GBF_CUDA(cudaMemcpyAsync(ws.hb_err_host, ws.hb_err, sizeof(int), cudaMemcpyDeviceToHost, st));
